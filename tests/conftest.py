@@ -1,0 +1,25 @@
+"""Shared test set-up: import path, the ``gpu`` marker, cached systems."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def pytest_configure(config):
+    config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
+
+
+@pytest.fixture(scope="session")
+def synth_cache():
+    import synth
+    cache = {}
+
+    def get(name):
+        if name not in cache:
+            cache[name] = synth.make_system(name)
+        return cache[name]
+    return get
