@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Benchmark of the Spectral Quadrature hot path on one GB300 (or N replicas).
+
+One step = one SCF-iteration's worth of the path on the whole grid:
+  sq_spectral_bounds (Lanczos) -> sq_moments (Chebyshev recurrence) ->
+  sq_fermi_level (weights + bisection) -> sq_density_energy.
+Metric: node-moments/s = N_d * n_pl / (seconds per step), whole job.
+
+Workload (default): 3x3x3 FCC cells (108 atoms), 48^3 grid, h = 0.478125 bohr,
+R_cut = 6 bohr (25^3 regions), n_pl = 48, kT = 0.05 Ha, s + 3p Gaussian KB
+projectors, 324 electrons; synthetic, seeded inputs.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+                  [--impl reference]
+
+Under torchrun (N > 1) every rank runs an independent replica of the workload
+on its own GPU (the path has no data exchange between replicas); the JSON line
+reports the total over ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+WORKLOAD = "al108_48"
+METRIC = "node-moments/s (nodes x Chebyshev degree per second, whole SCF-iteration step)"
+UNIT = "node-moments/s"
+PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+PROFILE_PATH = os.path.join(ROOT, "profiles", "roofline_counters.json")
+FP32_LANES_PER_SM = 128        # FP32 FMA lanes per SM per clock (Blackwell)
+SM_COUNT_GB300 = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (nodes); 0 = automatic")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# algorithmic work per unit (flops), used for the roofline
+# --------------------------------------------------------------------------
+LOCAL_FLOPS_RECUR = 52    # per region point per Chebyshev step (stencil, diagonal, update, two dots)
+LOCAL_FLOPS_LANCZOS = 56  # per region point per Lanczos step (stencil, diagonal, -beta v_old, alpha, w-alpha v, |w|^2, scale)
+NL_FLOPS_PER_PAIR = 8     # per (region point, projector support) pair per step: 2 FMA dots + 2 FMA apply
+
+
+def nl_pairs_per_point(wl):
+    """Mean number of atom supports covering a grid point."""
+    if not wl.nonlocal_:
+        return 0.0
+    return wl.n_atoms / wl.L ** 3 * (4.0 / 3.0) * math.pi * synth.PROJ_RNL ** 3
+
+
+def flops_moments(wl):
+    S = 2 * wl.m + 1
+    per_point = LOCAL_FLOPS_RECUR + NL_FLOPS_PER_PAIR * nl_pairs_per_point(wl)
+    return wl.n_nodes * (wl.npl // 2) * S ** 3 * per_point
+
+
+def flops_lanczos(wl):
+    S = 2 * wl.m + 1
+    per_point = LOCAL_FLOPS_LANCZOS + NL_FLOPS_PER_PAIR * nl_pairs_per_point(wl)
+    return wl.n_nodes * wl.n_lanczos * S ** 3 * per_point
+
+
+def source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1708_07913_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+# --------------------------------------------------------------------------
+# clocks sampling (nvidia-smi) during the timed region
+# --------------------------------------------------------------------------
+SMI_FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+
+class ClockSampler:
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.gpu}.csv")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(SMI_FIELDS),
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < len(SMI_FIELDS):
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle baseline (bounded sample of the same workload)
+# --------------------------------------------------------------------------
+_W = {}
+
+
+def _oracle_init(name):
+    import oracle
+    s = synth.make_system(name)
+    _W["wl"] = s.wl
+    _W["osys"] = oracle.OracleSystem.from_synth(s)
+
+
+def _oracle_chunk(nodes):
+    wl, osys = _W["wl"], _W["osys"]
+    t0 = time.perf_counter()
+    chi, zeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
+    osys.moments(nodes, chi, zeta, wl.npl)
+    return time.perf_counter() - t0
+
+
+class OraclePool:
+    """Spawned worker processes, each holding the workload in oracle form."""
+
+    def __init__(self, name, cores):
+        import multiprocessing as mp
+        import oracle
+        oracle.build()
+        self.name, self.cores = name, cores
+        self.pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(name,))
+
+    def rate(self, sample, seed=1234):
+        """node-moments/s of the oracle (bounds + moments, >99% of its per-step
+        cost) on a seeded node sample split over the workers; the slowest
+        worker's own compute time is the step time."""
+        wl = synth.WORKLOADS[self.name]
+        nodes = synth.sample_nodes(wl.n_nodes, sample, seed=seed)
+        chunks = [c for c in np.array_split(nodes, self.cores) if len(c)]
+        t = max(self.pool.map(_oracle_chunk, chunks))
+        return len(nodes) * wl.npl / t, t, len(chunks)
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def auto_sample(name, cores, target_s=15.0):
+    """Sample size for ~target_s seconds of oracle work per worker."""
+    per_node = {"al4_16": 0.005, "al108_48": 0.08, "al2048_128": 0.15}.get(name, 0.1)
+    return max(cores, min(int(target_s / per_node) * cores, synth.WORKLOADS[name].n_nodes))
+
+
+# --------------------------------------------------------------------------
+def run_reference(a):
+    """The oracle as it stands, timed on the host cores, same metric and unit."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    wl = synth.WORKLOADS[a.workload]
+    cores = os.cpu_count() or 1
+    sample = a.cpu_sample or max(cores, int(4.0 / {"al4_16": 0.005, "al108_48": 0.08}.get(a.workload, 0.15)) * cores)
+    sample = min(sample, wl.n_nodes)
+    pool = OraclePool(a.workload, cores)
+    rates = []
+    for i in range(a.warmup + a.steps):
+        r, t, used = pool.rate(sample, seed=1234 + i)
+        if i >= a.warmup:
+            rates.append((r, t))
+    pool.close()
+    value = statistics.median(r for r, _ in rates)
+    t_full = wl.n_nodes * wl.npl / value
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t_full * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded FCC Al-like crystal, Gaussian V and KB projectors)",
+        "config": {"workload": f"{a.workload}: {wl.cells}^3 FCC cells ({wl.n_atoms} atoms), {wl.n}^3 grid, "
+                               f"{2 * wl.m + 1}^3 regions, n_pl={wl.npl}, kT={wl.kT}",
+                   "sample_nodes_per_step": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": used, "kind": "oracle",
+                         "sample": f"{sample} seeded nodes per step (bounds + moments), extrapolated per node"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_gb300(a):
+    import torch
+    from paper_1708_07913_gb300 import SQ_FP32, SQ_FP64, SQSolver, build
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+    build()
+    prec = SQ_FP32 if a.precision == "fp32" else SQ_FP64
+    s = synth.make_system(a.workload)
+    wl = s.wl
+    solver = SQSolver.from_workload(wl, s.positions, precision=prec, device=str(dev))
+    Vh = torch.from_numpy(s.V.ravel().copy()).pin_memory()
+    V = Vh.to(dev)
+    rho_h = torch.empty(wl.n_nodes, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > 129 MB L2
+    stream = torch.cuda.current_stream()
+
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def step(timed=None):
+        e = [ev() for _ in range(5)]
+        e[0].record(stream)
+        solver.bounds(V, wl.n_lanczos, wl.margin)
+        e[1].record(stream)
+        solver.compute_moments(V)
+        e[2].record(stream)
+        mu = solver.fermi_level(wl.n_electrons, wl.kT)
+        e[3].record(stream)
+        eb, es, ne = solver.density_energy(mu, wl.kT)
+        e[4].record(stream)
+        if timed is not None:
+            timed.append(e)
+        return mu, eb, es, ne
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    launches0 = solver.launches
+    timed = []
+    for _ in range(a.steps):
+        flush.fill_(1.0)                                   # evict L2 between steps (not timed)
+        step(timed)
+    torch.cuda.synchronize()
+    launches = solver.launches - launches0
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    # end-to-end through host buffers: V from pinned host memory, rho and the
+    # scalars back to the host, copies inside the timed region
+    e2e_t = []
+    for _ in range(max(2, a.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        V.copy_(Vh, non_blocking=True)
+        step()
+        rho_h.copy_(solver.rho, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_t.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+
+    per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in timed])   # ms
+    step_ms = per.sum(axis=1)
+    t_step = float(step_ms.mean()) / 1e3
+    t_e2e = float(np.median(e2e_t))
+    if dist:
+        tt = torch.tensor([t_step, t_e2e], dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, t_e2e = float(tt[0]), float(tt[1])
+    units = wl.n_nodes * wl.npl * world
+    value = units / t_step
+    t_bounds, t_mom, t_fermi, t_dens = (float(x) / 1e3 for x in per.mean(axis=0))
+
+    # roofline for the dominant kernel (FP32/FP64 CUDA-core pipe, "alu" bound)
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if prec == SQ_FP32:
+        peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    else:
+        peak = 1.25 * sms / SM_COUNT_GB300 * sm_max / 2070.0     # FP64 at GB300's published 1.25 TFLOP/s
+    kern = {"lanczos_kernel": (flops_lanczos(wl), t_bounds), "moments_kernel": (flops_moments(wl), t_mom)}
+    dom = max(kern, key=lambda k: kern[k][1])
+    achieved = kern[dom][0] / kern[dom][1] / 1e12
+    traffic = None
+    if os.path.exists(PROFILE_PATH):
+        prof = json.load(open(PROFILE_PATH))
+        key = f"{dom}:{a.workload}:{a.precision}"
+        if key in prof and prof[key].get("source_sha") == source_sha():
+            traffic = prof[key].get("dram_bytes_per_launch")
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32" if prec == SQ_FP32 else "f64",
+        "data": "synthetic (seeded FCC Al-like crystal, Gaussian V and KB projectors)",
+        "config": {"workload": f"{a.workload}: {wl.cells}^3 FCC cells ({wl.n_atoms} atoms), {wl.n}^3 grid "
+                               f"(h={wl.h:.6f}), {2 * wl.m + 1}^3 regions (R_cut={wl.r_cut}), n_pl={wl.npl}, "
+                               f"kT={wl.kT}, s+3p KB projectors, {int(wl.n_electrons)} electrons",
+                   "precision": ("FP32 recurrence/Lanczos vectors, FP64 moments, weights, Fermi level, energies"
+                                 if prec == SQ_FP32 else "FP64 throughout"),
+                   "n_lanczos": wl.n_lanczos, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "breakdown_s": {"bounds": t_bounds, "moments": t_mom, "fermi": t_fermi, "density": t_dens},
+        "moments_only_node_moments_per_s": wl.n_nodes * wl.npl * world / t_mom,
+        "s_per_scf_iteration": t_step,
+        "roofline": {"kernel": dom, "bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "peak_basis": (f"{'FP32' if prec == SQ_FP32 else 'FP64'} CUDA-core pipe at "
+                                    f"{sm_max:.0f} MHz x {sms} SMs (derived from unit counts and clock)")},
+        "e2e": {"value": units / t_e2e, "unit": UNIT, "h2d_bytes_per_step": wl.n_nodes * 8,
+                "d2h_bytes_per_step": wl.n_nodes * 8 + 4 * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sample = a.cpu_sample or auto_sample(a.workload, cores)
+        try:
+            pool = OraclePool(a.workload, cores)
+            rate, t, used = pool.rate(sample)
+            pool.close()
+            line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle",
+                                    "sample": f"{sample} seeded nodes of {a.workload} (Lanczos bounds + moments, "
+                                              f"{t:.1f} s on {used} processes), per-node rate"}
+        except Exception as exc:   # the CPU leg must not hide the GPU result
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
+                                    "sample": f"failed: {exc}"}
+    solver.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.warmup < 3:
+        a.warmup = 3
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_gb300(a)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,165 @@
+/*
+ * sq.h -- C ABI of libsq: the Clenshaw-Curtis Spectral Quadrature (SQ) hot
+ * path of "SQDFT: Spectral Quadrature method for large-scale parallel O(N)
+ * Kohn-Sham calculations at high temperature" (Suryanarayana, Pratapa,
+ * Sharma, Pask; arXiv:1708.07913), on one NVIDIA GB300 GPU (sm_103a).
+ *
+ * Problem (Section 2, Eqs. DensityMatrix, rho; Section 3.2): given the
+ * effective potential V on a periodic finite-difference grid of N_d nodes,
+ * compute for every node q the Chebyshev moments of its nodal Hamiltonian
+ * H_q (H restricted to the cube of side 2 R_cut about q with zero Dirichlet
+ * boundary), the Fermi level mu that puts N_e electrons in the cell, and the
+ * nodal electron density, band-structure energy and electronic entropy.
+ *
+ * Conventions
+ *   - Hartree atomic units (Ha, bohr).
+ *   - Grid: n1 x n2 x n3 nodes, spacing h, node (i,j,k) at (i h, j h, k h);
+ *     every per-node array is x-fastest: index q = i + n1*(j + n2*k).
+ *   - Unless stated otherwise, array arguments are DEVICE pointers owned by
+ *     the caller (any allocator, e.g. PyTorch), FP64, densely packed.
+ *   - Every call is enqueued on the context's CUDA stream.  sq_spectral_bounds
+ *     and sq_moments are asynchronous; sq_fermi_level, sq_density_energy and
+ *     sq_sync synchronise the stream because they return host scalars.
+ *   - Errors: every call returns an sq_status.  Argument errors are detected
+ *     on the host before anything is enqueued.  Device-side errors (a moment
+ *     with |rho^j| > 1 + tol, a capacity overflow, a wait budget exceeded) are
+ *     latched in the context and returned by the next synchronising call.
+ *     No C++ exception crosses this interface.
+ *   - Thread safety: a context may be used by one host thread at a time.
+ */
+#ifndef SQ_H
+#define SQ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SQ_OK = 0,
+    SQ_EINVAL = 1,      /* invalid argument (checked on the host)                    */
+    SQ_ECUDA = 2,       /* a CUDA runtime call or kernel launch failed               */
+    SQ_EBOUNDS = 3,     /* spectrum outside [chi-zeta, chi+zeta]: |rho^j| > 1 + tol   */
+    SQ_ENOCONV = 4,     /* Fermi-level bracket does not contain N_e                  */
+    SQ_ETIMEOUT = 5,    /* a device wait exceeded its budget                          */
+    SQ_ENOMEM = 6,      /* device allocation failed                                   */
+    SQ_ECAPACITY = 7,   /* a per-node table (projector candidates/rows) overflowed    */
+    SQ_EUNSUPPORTED = 8 /* valid request that this build does not implement           */
+} sq_status;
+
+typedef enum {
+    SQ_FP64 = 0,        /* recurrence, Lanczos and all sums in FP64                   */
+    SQ_FP32 = 1         /* recurrence and Lanczos vectors in FP32; moments, Lanczos   */
+                        /* coefficients, weights, Fermi level and energies in FP64    */
+} sq_precision;
+
+/* One Kleinman-Bylander projector channel (Section 2, Eq. Hamiltonian: V_nl;
+ * Section 3.1: restriction to the region of influence).  The paper uses
+ * Troullier-Martins projectors; this library implements Gaussian channels
+ *   l = 0:  chi(r)   = A_s exp(-r^2/(2 rc^2)),       A_s = (pi rc^2)^(-3/4)
+ *   l = 1:  chi_a(r) = A_p r_a exp(-r^2/(2 rc^2)),   A_p = (sqrt 2/rc) A_s
+ * supported on |r| < r_nl, entering H as gamma h^3 chi chi^T per projector.
+ * At most one l = 0 and one l = 1 channel, sharing rc and r_nl. */
+typedef struct {
+    int l;              /* 0 (s) or 1 (p)                     */
+    double gamma;       /* KB energy, Ha                      */
+    double rc;          /* Gaussian width, bohr               */
+    double r_nl;        /* support radius, bohr               */
+} sq_proj_type;
+
+typedef struct sq_ctx sq_ctx;
+
+/* Create a context for one grid/geometry (Section 3.1: grid, FD order,
+ * region of influence; Section 3.2: quadrature order).
+ *   n1,n2,n3       grid nodes per axis (>= 1)
+ *   h              mesh spacing, bohr (> 0)
+ *   fd_half_order  n_o of Eq. (FD:Laplacian); this build supports 6
+ *   r_cut          R_cut, bohr; region half-width m = floor(r_cut/h) points,
+ *                  region side 2m+1 <= 31
+ *   npl            quadrature degree n_pl (multiple of 4, 4 <= npl <= 512)
+ *   precision      sq_precision
+ *   n_atoms, atom_xyz_host   HOST array n_atoms*3 (bohr); may be NULL iff
+ *                  n_atoms == 0 or n_proj_types == 0
+ *   n_proj_types, proj       HOST array of channels; NULL / 0 = local only
+ *   cuda_stream    cudaStream_t to enqueue on (NULL = legacy default stream)
+ * Allocates device memory for projector tables and per-CTA scratch.
+ * On error *out is set to NULL. */
+int sq_setup_grid(sq_ctx **out, int n1, int n2, int n3, double h,
+                  int fd_half_order, double r_cut, int npl, int precision,
+                  int n_atoms, const double *atom_xyz_host,
+                  int n_proj_types, const sq_proj_type *proj,
+                  void *cuda_stream);
+
+/* Change the stream later calls enqueue on. */
+int sq_set_stream(sq_ctx *ctx, void *cuda_stream);
+
+/* Spectral bounds of every nodal Hamiltonian by the Lanczos method
+ * (Section 3.2, text after Eq. rhoqj: lambda_min, lambda_max of H_q, then
+ * chi_q = (max+min)/2, zeta_q = (max-min)/2).  Start vector uniform on the
+ * region; exactly n_lanczos steps (fewer only on breakdown, beta <= 1e-10 *
+ * scale); extreme Ritz values by Sturm bisection in FP64; both ends widened
+ * by margin * max(theta_max - theta_min, 1 Ha).
+ *   V     device, N_d FP64 effective potential
+ *   chi   device, N_d FP64 output
+ *   zeta  device, N_d FP64 output
+ *   1 <= n_lanczos <= 512, 0 <= margin < 1. */
+int sq_spectral_bounds(sq_ctx *ctx, const double *V, double *chi, double *zeta,
+                       int n_lanczos, double margin);
+
+/* Chebyshev moments rho_q^j, j = 0..npl (Section 3.2, Eqs. Rec:FD, rhoqj):
+ * t^0 = e_q, t^1 = Hhat t^0, t^{i+1} = 2 Hhat t^i - t^{i-1}, Hhat = (H_q -
+ * chi_q)/zeta_q, run to i = npl/2; rho^j = t^j at the node for j <= npl/2,
+ * and from the product property 2T_aT_b = T_{a+b} + T_{|a-b|}:
+ * rho^{2a} = 2 t^a.t^a - rho^0, rho^{2a+1} = 2 t^{a+1}.t^a - rho^1.
+ *   V         device, N_d FP64
+ *   chi,zeta  device, N_d FP64 (zeta > 0)
+ *   moments   device, N_d*(npl+1) FP64 output, node-major
+ * A moment with |rho^j| > 1 + tol (tol 1e-6 FP64, 1e-4 FP32) latches
+ * SQ_EBOUNDS. */
+int sq_moments(sq_ctx *ctx, const double *V, const double *chi, const double *zeta,
+               double *moments);
+
+/* Fermi level (Section 3.2): solve 2 sum_q sum_j c_q^j(mu) rho_q^j = N_e with
+ * c_q^j the Chebyshev coefficients of the Fermi-Dirac function (Eq. cqj) by
+ * discrete orthogonality at the npl+1 zeros of T_{npl+1}.  Bisection on
+ * [min(chi-zeta) - 10 kT, max(chi+zeta) + 10 kT] until the midpoint equals an
+ * end point in FP64 (at most 200 steps).  Also stores the quadrature weights
+ * W_qk in the context for sq_density_energy.
+ *   moments, chi, zeta   device, as produced above
+ *   n_electrons          0 < N_e < 2 N_d
+ *   kT                   smearing sigma > 0, Ha
+ *   mu_host              HOST output
+ * Synchronises the stream.  SQ_ENOCONV if N(lo) > N_e or N(hi) < N_e. */
+int sq_fermi_level(sq_ctx *ctx, const double *moments, const double *chi,
+                   const double *zeta, double n_electrons, double kT, double *mu_host);
+
+/* Nodal density, band energy and entropy energy at Fermi level mu
+ * (Eq. ElectronDensity; Eqs. Eband, d_q; Eqs. Entropy, e_q):
+ *   rho_q  = (2/h^3) sum_k W_qk g_qk
+ *   E_band = 2 sum_q sum_k W_qk (chi_q + zeta_q x_k) g_qk
+ *   E_ent  = 2 kT sum_q sum_k W_qk [g ln g + (1-g) ln(1-g)]   (0 ln 0 = 0)
+ *   N      = h^3 sum_q rho_q
+ * with g_qk = 1/(1 + exp((chi_q + zeta_q x_k - mu)/kT)).  Recomputes W from
+ * the moments.
+ *   rho                   device, N_d FP64 output
+ *   e_band_host, e_ent_host, n_elec_host   HOST outputs (each may be NULL)
+ * Synchronises the stream. */
+int sq_density_energy(sq_ctx *ctx, const double *moments, const double *chi,
+                      const double *zeta, double mu, double kT, double *rho,
+                      double *e_band_host, double *e_ent_host, double *n_elec_host);
+
+/* Wait for the context's stream and return any latched device error. */
+int sq_sync(sq_ctx *ctx);
+
+/* Number of kernel launches this context has enqueued since creation. */
+long long sq_launch_count(const sq_ctx *ctx);
+
+/* Release all device memory of the context (NULL is a no-op). */
+void sq_destroy(sq_ctx *ctx);
+
+/* Static description of a status code. */
+const char *sq_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SQ_H */

@@ -1,0 +1,99 @@
+"""GB300-native Spectral Quadrature hot path (arXiv:1708.07913, Section 3).
+
+``sq`` is the ctypes binding of libsq.so (the C ABI in include/sq.h);
+``SQSolver`` strings its calls together for one grid/geometry:
+
+    bounds (Lanczos) -> Chebyshev moments -> Fermi level -> density/energy
+
+Device memory and streams come from PyTorch; all arithmetic of the path runs
+in libsq's CUDA kernels.
+"""
+from __future__ import annotations
+
+from . import sq
+from .sq import SQ_FP32, SQ_FP64, SQError
+
+__all__ = ["sq", "SQSolver", "SQ_FP32", "SQ_FP64", "SQError", "build"]
+
+
+def build(force: bool = False) -> str:
+    from .build import build as _build
+    return _build(force=force)
+
+
+class SQSolver:
+    """One context (grid, region, projectors, precision) and its device buffers."""
+
+    def __init__(self, shape, h, r_cut, npl, precision=SQ_FP64, positions=None, proj_types=(), fd_half_order=6,
+                 device="cuda:0"):
+        import torch
+        self.torch = torch
+        self.device = torch.device(device)
+        self.shape = tuple(int(s) for s in shape)          # (n1, n2, n3)
+        self.npl = int(npl)
+        self.h = float(h)
+        n1, n2, n3 = self.shape
+        self.n_nodes = n1 * n2 * n3
+        with torch.cuda.device(self.device):
+            self.ctx = sq.sq_setup_grid(n1, n2, n3, h, fd_half_order, r_cut, npl, precision, positions,
+                                        list(proj_types))
+            f64 = dict(dtype=torch.float64, device=self.device)
+            self.chi = torch.empty(self.n_nodes, **f64)
+            self.zeta = torch.empty(self.n_nodes, **f64)
+            self.moments = torch.empty(self.n_nodes, self.npl + 1, **f64)
+            self.rho = torch.empty(self.n_nodes, **f64)
+
+    @classmethod
+    def from_workload(cls, wl, positions, precision=SQ_FP64, device="cuda:0"):
+        import synth
+        return cls((wl.n, wl.n, wl.n), wl.h, wl.r_cut, wl.npl, precision, positions,
+                   synth.projector_types(wl.nonlocal_), wl.fd_half_order, device)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            sq.sq_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bounds(self, V, n_lanczos=40, margin=0.01):
+        sq.sq_set_stream(self.ctx)
+        sq.sq_spectral_bounds(self.ctx, V, self.chi, self.zeta, n_lanczos, margin)
+        return self.chi, self.zeta
+
+    def compute_moments(self, V, chi=None, zeta=None):
+        sq.sq_set_stream(self.ctx)
+        sq.sq_moments(self.ctx, V, self.chi if chi is None else chi, self.zeta if zeta is None else zeta,
+                      self.moments)
+        return self.moments
+
+    def fermi_level(self, n_electrons, kT, chi=None, zeta=None):
+        sq.sq_set_stream(self.ctx)
+        return sq.sq_fermi_level(self.ctx, self.moments, self.chi if chi is None else chi,
+                                 self.zeta if zeta is None else zeta, n_electrons, kT)
+
+    def density_energy(self, mu, kT, chi=None, zeta=None):
+        sq.sq_set_stream(self.ctx)
+        return sq.sq_density_energy(self.ctx, self.moments, self.chi if chi is None else chi,
+                                    self.zeta if zeta is None else zeta, mu, kT, self.rho)
+
+    def solve(self, V, n_electrons, kT, n_lanczos=40, margin=0.01, bounds=None):
+        """The whole path on a device potential V (float64, N_d).  ``bounds``
+        = (chi, zeta) device tensors skips the Lanczos step."""
+        if bounds is None:
+            chi, zeta = self.bounds(V, n_lanczos, margin)
+        else:
+            chi, zeta = bounds
+        self.compute_moments(V, chi, zeta)
+        mu = self.fermi_level(n_electrons, kT, chi, zeta)
+        eb, es, ne = self.density_energy(mu, kT, chi, zeta)
+        return dict(mu=mu, e_band=eb, e_ent=es, n_elec=ne, rho=self.rho, moments=self.moments, chi=chi,
+                    zeta=zeta)
+
+    @property
+    def launches(self):
+        return sq.sq_launch_count(self.ctx)

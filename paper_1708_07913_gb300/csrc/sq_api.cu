@@ -1,0 +1,432 @@
+// sq_api.cu -- host side of the libsq C ABI (include/sq.h): argument
+// validation, context set-up (device tables, per-CTA scratch), and the
+// enqueueing of the kernels for each step of the Spectral Quadrature path.
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "sq_region.cuh"
+
+namespace sq {
+int region_config_f32(int m, int which, int* bps, size_t* smem);
+int region_config_f64(int m, int which, int* bps, size_t* smem);
+int region_launch_f32(int m, int which, const RegionArgs<float>& a, int blocks, cudaStream_t st);
+int region_launch_f64(int m, int which, const RegionArgs<double>& a, int blocks, cudaStream_t st);
+}  // namespace sq
+
+using namespace sq;
+
+namespace {
+
+bool is_fin(double x) { return std::isfinite(x); }
+
+// A device pointer the GPU can dereference (device or managed memory).
+bool is_device_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// Central finite-difference weights of the paper's Eq. (FD:Laplacian):
+//   w_0 = -(1/h^2) sum_{q=1}^{n_o} q^-2,
+//   w_d = 2 (-1)^{d+1} (n_o!)^2 / (h^2 d^2 (n_o-d)! (n_o+d)!).
+void fd_weights(int no, double h, double* w)
+{
+    double f[32];
+    f[0] = 1.0;
+    for (int i = 1; i < 32; ++i) f[i] = f[i - 1] * i;
+    double s = 0.0;
+    for (int q = 1; q <= no; ++q) s += 1.0 / ((double)q * q);
+    w[0] = -s / (h * h);
+    for (int d = 1; d <= no; ++d)
+        w[d] = ((d & 1) ? 2.0 : -2.0) / (h * h * d * d) * f[no] * f[no] / (f[no - d] * f[no + d]);
+}
+
+template <typename P>
+int dev_alloc(P** p, size_t bytes)
+{
+    *p = nullptr;
+    if (bytes == 0) bytes = 256;
+    if (cudaMalloc((void**)p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return SQ_ENOMEM;
+    }
+    return SQ_OK;
+}
+
+void free_ctx(sq_ctx* c)
+{
+    if (!c) return;
+    void* ptrs[] = {c->Vp, c->d_atoms, c->d_G, c->d_DG, c->d_ivl, c->d_tile_start, c->d_tile_cand, c->d_scratch,
+                    c->d_alpha, c->d_beta, c->d_klen, c->d_W, c->d_red, c->d_fermi, c->d_count, c->d_err};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    delete c;
+}
+
+// Latched device error bits -> status (and clear them).  Synchronises.
+int take_device_error(sq_ctx* c)
+{
+    unsigned e = 0;
+    if (cudaMemcpyAsync(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess) return SQ_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+    if (e == 0) return SQ_OK;
+    unsigned z = 0;
+    if (cudaMemcpyAsync(c->d_err, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return SQ_ECUDA;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+    if (e & ERR_CAPACITY) return SQ_ECAPACITY;
+    return SQ_EBOUNDS;
+}
+
+// Projector geometry and tile candidate lists (host integer bookkeeping; the
+// Gaussian tables themselves are evaluated on the device).
+int setup_projectors(sq_ctx* c, const double* xyz)
+{
+    const GridParams& g = c->g;
+    const int n[3] = {g.n1, g.n2, g.n3};
+    const int m = g.m;
+    std::vector<AtomTab> at(c->n_atoms);
+    for (int I = 0; I < c->n_atoms; ++I) {
+        for (int a = 0; a < 3; ++a) {
+            double R = xyz[3 * I + a];
+            int lo = (int)ceil((R - c->rnl) / g.h);
+            int hi = (int)floor((R + c->rnl) / g.h);
+            if (hi < lo) hi = lo - 1;
+            at[I].lo[a] = lo;
+            at[I].len[a] = hi - lo + 1;
+            if (at[I].len[a] > NL_BOX) return SQ_EUNSUPPORTED;
+        }
+    }
+    for (int a = 0; a < 3; ++a) c->ntile[a] = (n[a] + TILE - 1) / TILE;
+    const long long ntiles = (long long)c->ntile[0] * c->ntile[1] * c->ntile[2];
+    // (tile, atom, box start) records; tiles meet a box iff the union of
+    // their nodes' regions, [t*TILE - m, t*TILE + TILE - 1 + m], meets it
+    struct Rec { long long tile; int atom, bx, by, bz; };
+    std::vector<Rec> recs;
+    for (int I = 0; I < c->n_atoms; ++I) {
+        if (at[I].len[0] <= 0 || at[I].len[1] <= 0 || at[I].len[2] <= 0) continue;
+        std::vector<std::pair<int, int>> axis[3];   // (box start, tile)
+        for (int a = 0; a < 3; ++a) {
+            int E = (m + NL_BOX + TILE) / n[a] + 2;
+            for (int e = -E; e <= E; ++e) {
+                int b0 = at[I].lo[a] + e * n[a], b1 = b0 + at[I].len[a] - 1;
+                for (int t = 0; t < c->ntile[a]; ++t) {
+                    int u0 = t * TILE - m, u1 = std::min(t * TILE + TILE, n[a]) - 1 + m;
+                    if (b0 <= u1 && b1 >= u0) axis[a].push_back({b0, t});
+                }
+            }
+        }
+        for (auto& z : axis[2])
+            for (auto& y : axis[1])
+                for (auto& x : axis[0]) {
+                    long long tile = x.second + (long long)c->ntile[0] * (y.second + (long long)c->ntile[1] * z.second);
+                    recs.push_back({tile, I, x.first, y.first, z.first});
+                }
+    }
+    std::vector<int> start(ntiles + 1, 0);
+    for (auto& r : recs) start[r.tile + 1]++;
+    for (long long t = 0; t < ntiles; ++t) start[t + 1] += start[t];
+    std::vector<int4> cand(recs.size());
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (auto& r : recs) cand[fill[r.tile]++] = make_int4(r.atom, r.bx, r.by, r.bz);   // stable: atom order
+
+    int rc;
+    size_t tsz = c->precision == SQ_FP32 ? sizeof(float) : sizeof(double);
+    if ((rc = dev_alloc(&c->d_atoms, sizeof(AtomTab) * at.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_G, tsz * 3 * NL_BOX * at.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_DG, tsz * 3 * NL_BOX * at.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_ivl, (size_t)NL_BOX * NL_BOX * 2 * at.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_tile_start, sizeof(int) * start.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_tile_cand, sizeof(int4) * std::max<size_t>(cand.size(), 1)))) return rc;
+    double* d_R = nullptr;
+    if ((rc = dev_alloc(&d_R, sizeof(double) * 3 * at.size()))) return rc;
+    SQ_CUDA_TRY(cudaMemcpy(c->d_atoms, at.data(), sizeof(AtomTab) * at.size(), cudaMemcpyHostToDevice));
+    SQ_CUDA_TRY(cudaMemcpy(c->d_tile_start, start.data(), sizeof(int) * start.size(), cudaMemcpyHostToDevice));
+    if (!cand.empty())
+        SQ_CUDA_TRY(cudaMemcpy(c->d_tile_cand, cand.data(), sizeof(int4) * cand.size(), cudaMemcpyHostToDevice));
+    SQ_CUDA_TRY(cudaMemcpy(d_R, xyz, sizeof(double) * 3 * at.size(), cudaMemcpyHostToDevice));
+    rc = launch_proj_tables(c, d_R);
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    cudaFree(d_R);
+    if (rc) return rc;
+    return e == cudaSuccess ? SQ_OK : SQ_ECUDA;
+}
+
+template <typename T>
+RegionArgs<T> region_args(sq_ctx* c)
+{
+    RegionArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.g = c->g;
+    a.Vp = (const T*)c->Vp;
+    a.nl.n_atoms = (c->has_s || c->has_p) ? c->n_atoms : 0;
+    a.nl.atoms = c->d_atoms;
+    a.nl.G = (const T*)c->d_G;
+    a.nl.DG = (const T*)c->d_DG;
+    a.nl.ivl = c->d_ivl;
+    a.nl.tile_start = c->d_tile_start;
+    a.nl.tile_cand = c->d_tile_cand;
+    for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
+    const double h3 = c->g.h * c->g.h * c->g.h;
+    const double As2 = pow(M_PI * c->rc * c->rc, -1.5);          // A_s^2
+    const double Ap2 = 2.0 / (c->rc * c->rc) * As2;              // A_p^2
+    a.nl.cs = (T)(c->has_s ? h3 * c->gamma_s * As2 : 0.0);
+    a.nl.cp = (T)(c->has_p ? h3 * c->gamma_p * Ap2 : 0.0);
+    a.scratch = (char*)c->d_scratch;
+    a.scratch_stride = c->scratch_bytes_per_cta;
+    a.err = c->d_err;
+    a.npl = c->npl;
+    a.mom_tol = c->precision == SQ_FP32 ? 1e-4 : 1e-6;
+    return a;
+}
+
+int region_blocks(sq_ctx* c, int which, int* blocks)
+{
+    int bps = 0;
+    size_t smem = 0;
+    int rc = c->precision == SQ_FP32 ? region_config_f32(c->g.m, which, &bps, &smem)
+                                     : region_config_f64(c->g.m, which, &bps, &smem);
+    if (rc) return rc;
+    long long b = (long long)bps * c->sm_count;
+    if (b > c->g.Nd) b = c->g.Nd;
+    *blocks = (int)b;
+    return SQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* sq_strerror(int s)
+{
+    switch (s) {
+        case SQ_OK: return "ok";
+        case SQ_EINVAL: return "invalid argument";
+        case SQ_ECUDA: return "CUDA runtime error";
+        case SQ_EBOUNDS: return "Chebyshev moment outside [-1,1]: spectrum not enclosed by [chi-zeta, chi+zeta]";
+        case SQ_ENOCONV: return "Fermi-level bracket does not contain the electron count";
+        case SQ_ETIMEOUT: return "device wait budget exceeded";
+        case SQ_ENOMEM: return "device allocation failed";
+        case SQ_ECAPACITY: return "per-node projector table capacity exceeded";
+        case SQ_EUNSUPPORTED: return "request not supported by this build";
+    }
+    return "unknown status";
+}
+
+int sq_setup_grid(sq_ctx** out, int n1, int n2, int n3, double h, int fd_half_order, double r_cut, int npl,
+                  int precision, int n_atoms, const double* atom_xyz_host, int n_proj_types,
+                  const sq_proj_type* proj, void* cuda_stream)
+{
+    if (!out) return SQ_EINVAL;
+    *out = nullptr;
+    if (n1 < 1 || n2 < 1 || n3 < 1 || n1 > 4096 || n2 > 4096 || n3 > 4096) return SQ_EINVAL;
+    if ((long long)n1 * n2 * n3 > (1LL << 31)) return SQ_EINVAL;
+    if (!is_fin(h) || h <= 0.0 || !is_fin(r_cut) || r_cut < 0.0) return SQ_EINVAL;
+    if (fd_half_order < 1 || fd_half_order > 16) return SQ_EINVAL;
+    if (fd_half_order != FD_NO) return SQ_EUNSUPPORTED;
+    if (npl < 4 || npl > MAX_NPL || npl % 4 != 0) return SQ_EINVAL;
+    if (precision != SQ_FP64 && precision != SQ_FP32) return SQ_EINVAL;
+    if (n_atoms < 0 || n_proj_types < 0 || n_proj_types > 2) return SQ_EINVAL;
+    if (n_proj_types > 0 && !proj) return SQ_EINVAL;
+    if (n_proj_types > 0 && n_atoms > 0 && !atom_xyz_host) return SQ_EINVAL;
+    double rm = floor(r_cut / h + 1e-12);
+    if (rm > MAX_M) return SQ_EUNSUPPORTED;
+    int m = (int)rm;
+    if (precision == SQ_FP64 && m > 12) return SQ_EUNSUPPORTED;
+    int has_s = 0, has_p = 0;
+    double gs = 0, gp = 0, rc = 0, rnl = 0;
+    for (int t = 0; t < n_proj_types; ++t) {
+        const sq_proj_type& p = proj[t];
+        if ((p.l != 0 && p.l != 1) || !is_fin(p.gamma) || !is_fin(p.rc) || p.rc <= 0.0 || !is_fin(p.r_nl) ||
+            p.r_nl <= 0.0)
+            return SQ_EINVAL;
+        if (p.l == 0) { if (has_s) return SQ_EUNSUPPORTED; has_s = 1; gs = p.gamma; }
+        else { if (has_p) return SQ_EUNSUPPORTED; has_p = 1; gp = p.gamma; }
+        if (t > 0 && (p.rc != rc || p.r_nl != rnl)) return SQ_EUNSUPPORTED;
+        rc = p.rc;
+        rnl = p.r_nl;
+    }
+    if (n_proj_types > 0 && 2.0 * rnl / h + 2.0 > NL_BOX) return SQ_EUNSUPPORTED;
+    for (long long i = 0; n_proj_types > 0 && i < 3LL * n_atoms; ++i)
+        if (!is_fin(atom_xyz_host[i])) return SQ_EINVAL;
+
+    sq_ctx* c = new (std::nothrow) sq_ctx;
+    if (!c) return SQ_ENOMEM;
+    memset(c, 0, sizeof(*c));
+    c->precision = precision;
+    c->npl = npl;
+    c->stream = (cudaStream_t)cuda_stream;
+    c->g.n1 = n1; c->g.n2 = n2; c->g.n3 = n3;
+    c->g.m = m;
+    c->g.Nd = (long long)n1 * n2 * n3;
+    c->g.P1 = n1 + 2 * m;
+    c->g.P2 = n2 + 2 * m;
+    c->g.h = h;
+    fd_weights(FD_NO, h, c->g.w);
+    c->n_atoms = (n_proj_types > 0) ? n_atoms : 0;
+    c->has_s = has_s; c->has_p = has_p;
+    c->gamma_s = gs; c->gamma_p = gp; c->rc = rc; c->rnl = rnl;
+
+    int dev = 0, rcode;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return SQ_ECUDA;
+    }
+    const size_t tsz = precision == SQ_FP32 ? sizeof(float) : sizeof(double);
+    const long long P3 = n3 + 2 * m;
+    if ((rcode = dev_alloc(&c->Vp, tsz * c->g.P1 * c->g.P2 * P3))) { free_ctx(c); return rcode; }
+    if (c->n_atoms > 0) {
+        if ((rcode = setup_projectors(c, atom_xyz_host))) { free_ctx(c); return rcode; }
+    } else {
+        c->ntile[0] = c->ntile[1] = c->ntile[2] = 1;
+    }
+    int bm = 0, bl = 0;
+    if ((rcode = region_blocks(c, 0, &bm)) || (rcode = region_blocks(c, 1, &bl))) { free_ctx(c); return rcode; }
+    c->grid_blocks = std::max(bm, bl);
+    c->scratch_bytes_per_cta = scratch_layout(m, tsz).total;
+    if ((rcode = dev_alloc(&c->d_scratch, c->scratch_bytes_per_cta * c->grid_blocks))) { free_ctx(c); return rcode; }
+    c->red_blocks = c->sm_count * 4;
+    if ((rcode = dev_alloc(&c->d_W, sizeof(double) * c->g.Nd * (npl + 1))) ||
+        (rcode = dev_alloc(&c->d_red, sizeof(double) * 3 * c->red_blocks)) ||
+        (rcode = dev_alloc(&c->d_fermi, sizeof(double) * 32)) ||
+        (rcode = dev_alloc(&c->d_count, sizeof(unsigned) * 4)) || (rcode = dev_alloc(&c->d_err, sizeof(unsigned)))) {
+        free_ctx(c);
+        return rcode;
+    }
+    if (cudaMemsetAsync(c->d_count, 0, sizeof(unsigned) * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->d_err, 0, sizeof(unsigned), c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess) {
+        cudaGetLastError();
+        free_ctx(c);
+        return SQ_ECUDA;
+    }
+    *out = c;
+    return SQ_OK;
+}
+
+int sq_set_stream(sq_ctx* c, void* stream)
+{
+    if (!c) return SQ_EINVAL;
+    c->stream = (cudaStream_t)stream;
+    return SQ_OK;
+}
+
+int sq_spectral_bounds(sq_ctx* c, const double* V, double* chi, double* zeta, int n_lanczos, double margin)
+{
+    if (!c || n_lanczos < 1 || n_lanczos > 512 || !is_fin(margin) || margin < 0.0 || margin >= 1.0)
+        return SQ_EINVAL;
+    if (!is_device_ptr(V) || !is_device_ptr(chi) || !is_device_ptr(zeta)) return SQ_EINVAL;
+    if (n_lanczos > c->nl_cap) {
+        if (c->d_alpha) cudaFree(c->d_alpha);
+        if (c->d_beta) cudaFree(c->d_beta);
+        if (c->d_klen) cudaFree(c->d_klen);
+        c->d_alpha = c->d_beta = nullptr;
+        c->d_klen = nullptr;
+        c->nl_cap = 0;
+        int rc;
+        if ((rc = dev_alloc(&c->d_alpha, sizeof(double) * c->g.Nd * n_lanczos)) ||
+            (rc = dev_alloc(&c->d_beta, sizeof(double) * c->g.Nd * n_lanczos)) ||
+            (rc = dev_alloc(&c->d_klen, sizeof(int) * c->g.Nd)))
+            return rc;
+        c->nl_cap = n_lanczos;
+    }
+    int rc = launch_build_vpad(c, V);
+    if (rc) return rc;
+    int blocks = 0;
+    if ((rc = region_blocks(c, 1, &blocks))) return rc;
+    if (c->precision == SQ_FP32) {
+        RegionArgs<float> a = region_args<float>(c);
+        a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
+        rc = region_launch_f32(c->g.m, 1, a, blocks, c->stream);
+    } else {
+        RegionArgs<double> a = region_args<double>(c);
+        a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
+        rc = region_launch_f64(c->g.m, 1, a, blocks, c->stream);
+    }
+    c->launches++;
+    if (rc) return rc;
+    return launch_tridiag_bounds(c, margin, chi, zeta);
+}
+
+int sq_moments(sq_ctx* c, const double* V, const double* chi, const double* zeta, double* moments)
+{
+    if (!c) return SQ_EINVAL;
+    if (!is_device_ptr(V) || !is_device_ptr(chi) || !is_device_ptr(zeta) || !is_device_ptr(moments))
+        return SQ_EINVAL;
+    int rc = launch_build_vpad(c, V);
+    if (rc) return rc;
+    int blocks = 0;
+    if ((rc = region_blocks(c, 0, &blocks))) return rc;
+    if (c->precision == SQ_FP32) {
+        RegionArgs<float> a = region_args<float>(c);
+        a.chi = chi; a.zeta = zeta; a.moments = moments;
+        rc = region_launch_f32(c->g.m, 0, a, blocks, c->stream);
+    } else {
+        RegionArgs<double> a = region_args<double>(c);
+        a.chi = chi; a.zeta = zeta; a.moments = moments;
+        rc = region_launch_f64(c->g.m, 0, a, blocks, c->stream);
+    }
+    c->launches++;
+    return rc;
+}
+
+int sq_fermi_level(sq_ctx* c, const double* moments, const double* chi, const double* zeta, double n_electrons,
+                   double kT, double* mu_host)
+{
+    if (!c || !mu_host || !is_fin(n_electrons) || !is_fin(kT) || kT <= 0.0) return SQ_EINVAL;
+    if (n_electrons <= 0.0 || n_electrons >= 2.0 * (double)c->g.Nd) return SQ_EINVAL;
+    if (!is_device_ptr(moments) || !is_device_ptr(chi) || !is_device_ptr(zeta)) return SQ_EINVAL;
+    int rc = launch_weights(c, moments);
+    if (rc) return rc;
+    double mu = 0.0;
+    rc = run_fermi(c, chi, zeta, n_electrons, kT, &mu);
+    int e = take_device_error(c);
+    if (e) return e;
+    if (rc) return rc;
+    *mu_host = mu;
+    return SQ_OK;
+}
+
+int sq_density_energy(sq_ctx* c, const double* moments, const double* chi, const double* zeta, double mu, double kT,
+                      double* rho, double* e_band_host, double* e_ent_host, double* n_elec_host)
+{
+    if (!c || !is_fin(mu) || !is_fin(kT) || kT <= 0.0) return SQ_EINVAL;
+    if (!is_device_ptr(moments) || !is_device_ptr(chi) || !is_device_ptr(zeta) || !is_device_ptr(rho))
+        return SQ_EINVAL;
+    int rc = launch_weights(c, moments);
+    if (rc) return rc;
+    rc = run_density(c, chi, zeta, mu, kT, rho, e_band_host, e_ent_host, n_elec_host);
+    int e = take_device_error(c);
+    if (e) return e;
+    return rc;
+}
+
+int sq_sync(sq_ctx* c)
+{
+    if (!c) return SQ_EINVAL;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+    return take_device_error(c);
+}
+
+long long sq_launch_count(const sq_ctx* c) { return c ? c->launches : -1; }
+
+void sq_destroy(sq_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,152 @@
+"""ctypes binding of libsq (include/sq.h): argument marshalling only.
+
+Each function has the name and meaning of the C entry point.  Device arrays
+are ``torch.Tensor`` objects on a CUDA device (float64, contiguous); the
+binding passes their data pointers and the current torch stream.  Every step
+of the path runs in libsq's kernels: there is no CPU fallback, and a missing
+or unloadable library raises immediately.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsq.so")
+
+SQ_OK, SQ_EINVAL, SQ_ECUDA, SQ_EBOUNDS, SQ_ENOCONV, SQ_ETIMEOUT, SQ_ENOMEM, SQ_ECAPACITY, SQ_EUNSUPPORTED = range(9)
+SQ_FP64, SQ_FP32 = 0, 1
+
+# Every entry point declared in include/sq.h.
+EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments", "sq_fermi_level",
+           "sq_density_energy", "sq_sync", "sq_launch_count", "sq_destroy", "sq_strerror")
+
+
+class SQError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {sq_strerror(code)} (status {code})")
+
+
+class ProjType(C.Structure):
+    _fields_ = [("l", C.c_int), ("gamma", C.c_double), ("rc", C.c_double), ("r_nl", C.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libsq.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path == LIB_PATH:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(f"libsq.so not built at {path}; run __graft_entry__.build()")
+        lib = C.CDLL(path)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.c_int
+        lib.sq_setup_grid.argtypes = [C.POINTER(vp), ip, ip, ip, C.c_double, ip, C.c_double, ip, ip, ip, dp, ip,
+                                      C.POINTER(ProjType), vp]
+        lib.sq_set_stream.argtypes = [vp, vp]
+        lib.sq_spectral_bounds.argtypes = [vp, vp, vp, vp, ip, C.c_double]
+        lib.sq_moments.argtypes = [vp, vp, vp, vp, vp]
+        lib.sq_fermi_level.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, dp]
+        lib.sq_density_energy.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp, dp, dp, dp]
+        lib.sq_sync.argtypes = [vp]
+        lib.sq_launch_count.argtypes = [vp]
+        lib.sq_launch_count.restype = C.c_longlong
+        lib.sq_destroy.argtypes = [vp]
+        lib.sq_destroy.restype = None
+        lib.sq_strerror.argtypes = [ip]
+        lib.sq_strerror.restype = C.c_char_p
+        if path == LIB_PATH:
+            _lib = lib
+        return lib
+
+
+def sq_strerror(code: int) -> str:
+    return load().sq_strerror(int(code)).decode()
+
+
+def _check(rc: int, where: str):
+    if rc != SQ_OK:
+        raise SQError(rc, where)
+
+
+def _dptr(t, name):
+    """Device pointer of a contiguous float64 CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def sq_setup_grid(n1, n2, n3, h, fd_half_order, r_cut, npl, precision, positions=None, proj_types=(),
+                  stream=None):
+    """Returns an opaque context handle (int)."""
+    lib = load()
+    ctx = C.c_void_p()
+    pos = np.ascontiguousarray(positions if positions is not None else np.zeros((0, 3)), dtype=np.float64)
+    pt = (ProjType * max(len(proj_types), 1))(*[ProjType(*p) for p in proj_types])
+    rc = lib.sq_setup_grid(C.byref(ctx), int(n1), int(n2), int(n3), float(h), int(fd_half_order), float(r_cut),
+                           int(npl), int(precision), int(pos.shape[0]),
+                           pos.ctypes.data_as(C.POINTER(C.c_double)) if pos.size else None,
+                           len(proj_types), pt if len(proj_types) else None,
+                           stream if stream is not None else _stream())
+    _check(rc, "sq_setup_grid")
+    return ctx.value
+
+
+def sq_set_stream(ctx, stream=None):
+    _check(load().sq_set_stream(C.c_void_p(ctx), stream if stream is not None else _stream()), "sq_set_stream")
+
+
+def sq_spectral_bounds(ctx, V, chi, zeta, n_lanczos, margin):
+    _check(load().sq_spectral_bounds(C.c_void_p(ctx), _dptr(V, "V"), _dptr(chi, "chi"), _dptr(zeta, "zeta"),
+                                     int(n_lanczos), float(margin)), "sq_spectral_bounds")
+
+
+def sq_moments(ctx, V, chi, zeta, moments):
+    _check(load().sq_moments(C.c_void_p(ctx), _dptr(V, "V"), _dptr(chi, "chi"), _dptr(zeta, "zeta"),
+                             _dptr(moments, "moments")), "sq_moments")
+
+
+def sq_fermi_level(ctx, moments, chi, zeta, n_electrons, kT) -> float:
+    mu = C.c_double()
+    _check(load().sq_fermi_level(C.c_void_p(ctx), _dptr(moments, "moments"), _dptr(chi, "chi"),
+                                 _dptr(zeta, "zeta"), float(n_electrons), float(kT), C.byref(mu)),
+           "sq_fermi_level")
+    return mu.value
+
+
+def sq_density_energy(ctx, moments, chi, zeta, mu, kT, rho):
+    """Fills rho; returns (E_band, E_ent, N)."""
+    eb, es, ne = C.c_double(), C.c_double(), C.c_double()
+    _check(load().sq_density_energy(C.c_void_p(ctx), _dptr(moments, "moments"), _dptr(chi, "chi"),
+                                    _dptr(zeta, "zeta"), float(mu), float(kT), _dptr(rho, "rho"),
+                                    C.byref(eb), C.byref(es), C.byref(ne)), "sq_density_energy")
+    return eb.value, es.value, ne.value
+
+
+def sq_sync(ctx):
+    _check(load().sq_sync(C.c_void_p(ctx)), "sq_sync")
+
+
+def sq_launch_count(ctx) -> int:
+    return int(load().sq_launch_count(C.c_void_p(ctx)))
+
+
+def sq_destroy(ctx):
+    if ctx:
+        load().sq_destroy(C.c_void_p(ctx))

@@ -1,0 +1,213 @@
+"""GPU path vs the CPU oracle, element by element, through the C ABI.
+
+Tolerances (from the target accuracy of the path):
+  FP64: density, Fermi level and energies within 1e-10 relative; moments
+        within 1e-11 absolute (they are bounded by 1); spectral bounds within
+        1e-9 relative (a fixed-count Lanczos run in two summation orders).
+  FP32 recurrence (FP64 moments/weights/Fermi level): density within 1e-5
+        relative (2-norm, and max-norm relative to max rho), energy within
+        1e-5 Ha/atom, moments within 2e-5 absolute.
+Oracle expected values never depend on the GPU; where the GPU must use the
+oracle's spectral bounds (to isolate the recurrence), they are copied from
+the oracle to the GPU, never the reverse."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1708_07913_gb300 import SQ_FP32, SQ_FP64, SQError, SQSolver, build, sq  # noqa: E402
+
+build()
+DEV = "cuda:0"
+FP64_RHO, FP64_MOM, FP64_BOUNDS = 1e-10, 1e-11, 1e-9
+FP32_RHO, FP32_MOM, FP32_E_PER_ATOM = 1e-5, 2e-5, 1e-5
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(DEV)
+
+
+def _rel2(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+@pytest.fixture(scope="module")
+def al4():
+    s = synth.make_system("al4_16")
+    wl = s.wl
+    ref = oracle.solve(oracle.OracleSystem.from_synth(s), wl.npl, wl.kT, wl.n_electrons, wl.n_lanczos, wl.margin)
+    return s, ref
+
+
+def _run(s, precision, bounds=None):
+    wl = s.wl
+    solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=DEV)
+    V = _dev(s.V)
+    b = None if bounds is None else (_dev(bounds[0]), _dev(bounds[1]))
+    out = solver.solve(V, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin, bounds=b)
+    torch.cuda.synchronize()
+    res = {k: (v.cpu().numpy().copy() if torch.is_tensor(v) else v) for k, v in out.items()}
+    solver.close()
+    return res
+
+
+def test_al4_fp64_full_path_matches_oracle(al4):
+    s, ref = al4
+    g = _run(s, SQ_FP64)
+    np.testing.assert_allclose(g["chi"], ref["chi"], rtol=FP64_BOUNDS)
+    np.testing.assert_allclose(g["zeta"], ref["zeta"], rtol=FP64_BOUNDS)
+    np.testing.assert_allclose(g["moments"], ref["moments"], rtol=0, atol=1e-9)
+    assert abs(g["mu"] - ref["mu"]) < FP64_RHO * max(1.0, abs(ref["mu"]))
+    assert _rel2(g["rho"], ref["rho"]) < FP64_RHO
+    assert np.abs(g["rho"] - ref["rho"]).max() < FP64_RHO * ref["rho"].max()
+    for k in ("e_band", "e_ent", "n_elec"):
+        assert abs(g[k] - ref[k]) < FP64_RHO * abs(ref[k]), k
+
+
+def test_al4_fp64_moments_with_oracle_bounds(al4):
+    s, ref = al4
+    g = _run(s, SQ_FP64, bounds=(ref["chi"], ref["zeta"]))
+    np.testing.assert_allclose(g["moments"], ref["moments"], rtol=0, atol=FP64_MOM)
+    assert _rel2(g["rho"], ref["rho"]) < FP64_RHO
+
+
+def test_al4_fp32_matches_oracle(al4):
+    s, ref = al4
+    g = _run(s, SQ_FP32, bounds=(ref["chi"], ref["zeta"]))
+    np.testing.assert_allclose(g["moments"], ref["moments"], rtol=0, atol=FP32_MOM)
+    assert _rel2(g["rho"], ref["rho"]) < FP32_RHO
+    assert np.abs(g["rho"] - ref["rho"]).max() < FP32_RHO * ref["rho"].max()
+    n_at = s.wl.n_atoms
+    assert abs(g["e_band"] - ref["e_band"]) / n_at < FP32_E_PER_ATOM
+    assert abs(g["e_ent"] - ref["e_ent"]) / n_at < FP32_E_PER_ATOM
+
+
+def test_al4_fp32_own_bounds(al4):
+    s, ref = al4
+    g = _run(s, SQ_FP32)
+    np.testing.assert_allclose(g["chi"], ref["chi"], rtol=1e-5)
+    np.testing.assert_allclose(g["zeta"], ref["zeta"], rtol=1e-5)
+    assert _rel2(g["rho"], ref["rho"]) < 10 * FP32_RHO
+    assert abs(g["n_elec"] - s.wl.n_electrons) < 1e-9 * s.wl.n_electrons
+
+
+@pytest.mark.parametrize("name,precision,count", [
+    ("al108_48", SQ_FP64, 12), ("al108_48", SQ_FP32, 24), ("al2048_128", SQ_FP32, 8)])
+def test_full_size_sampled_nodes(name, precision, count):
+    """Full-size workload in the benchmark's launch configuration; the oracle
+    recomputes bounds and moments of a seeded node sample one by one."""
+    s = synth.make_system(name)
+    wl = s.wl
+    nodes = synth.sample_nodes(wl.n_nodes, count, seed=11)
+    osys = oracle.OracleSystem.from_synth(s)
+    ochi, ozeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
+    omom = osys.moments(nodes, ochi, ozeta, wl.npl)
+    solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=DEV)
+    V = _dev(s.V)
+    chi, zeta = solver.bounds(V, wl.n_lanczos, wl.margin)
+    gchi, gzeta = chi.cpu().numpy()[nodes], zeta.cpu().numpy()[nodes]
+    tol_b = FP64_BOUNDS if precision == SQ_FP64 else 1e-5
+    np.testing.assert_allclose(gchi, ochi, rtol=tol_b)
+    np.testing.assert_allclose(gzeta, ozeta, rtol=tol_b)
+    # moments with the oracle's bounds on the sampled nodes
+    chi2, zeta2 = chi.clone(), zeta.clone()
+    idx = torch.from_numpy(nodes).to(DEV)
+    chi2[idx] = _dev(ochi)
+    zeta2[idx] = _dev(ozeta)
+    mom = solver.compute_moments(V, chi2, zeta2)
+    gm = mom.cpu().numpy()[nodes]
+    np.testing.assert_allclose(gm, omom, rtol=0, atol=FP64_MOM if precision == SQ_FP64 else FP32_MOM)
+    # whole-grid properties at full size
+    mu = solver.fermi_level(wl.n_electrons, wl.kT, chi2, zeta2)
+    eb, es, ne = solver.density_energy(mu, wl.kT, chi2, zeta2)
+    assert abs(ne - wl.n_electrons) < 1e-8 * wl.n_electrons
+    assert es <= 0.0
+    assert np.all(np.abs(mom.cpu().numpy()) <= 1 + 1e-6)
+    # density of the sampled nodes from the oracle's own moments at the GPU's mu
+    # is not an oracle-only expectation, so the density itself is checked on
+    # the small workloads; here only its integral and sign
+    assert torch.all(solver.rho >= -1e-8).item()
+    solver.close()
+
+
+@pytest.mark.parametrize("shape,r_cut,npl,nonlocal_", [
+    ((9, 12, 7), 3.5, 8, True),      # rectangular grid, region (9 points) wider than the cell in z
+    ((6, 6, 6), 0.1, 4, False),      # m = 0: one-point regions
+    ((5, 7, 6), 1.6, 12, True),      # m = 1
+    ((10, 10, 10), 3.0, 24, True),   # m = 3 with projectors
+])
+def test_edge_geometries_fp64_and_fp32(shape, r_cut, npl, nonlocal_):
+    n1, n2, n3 = shape
+    pos = synth.fcc_positions(1, 0.3, 77)
+    L = synth.LATTICE_A
+    h = L / n1
+    # a cell of n1 x n2 x n3 points of spacing h; atoms scaled into it
+    Ls = np.array([n1, n2, n3]) * h
+    pos = np.mod(pos / L * Ls, Ls)
+    rng = np.random.default_rng(5)
+    V = -1.5 + 0.5 * rng.standard_normal((n3, n2, n1))
+    m = int(np.floor(r_cut / h + 1e-12))
+    pt = synth.projector_types(nonlocal_)
+    osys = oracle.OracleSystem(V, h, m, pos, pt)
+    nodes = np.arange(n1 * n2 * n3)
+    Ne = 0.3 * nodes.size
+    ref = oracle.solve(osys, npl, 0.2, Ne, 20, 0.01)
+    for prec, rtol in ((SQ_FP64, FP64_RHO), (SQ_FP32, 1e-4)):
+        solver = SQSolver(shape, h, r_cut, npl, prec, pos, pt, device=DEV)
+        Vd = _dev(V)
+        chi, zeta = _dev(ref["chi"]), _dev(ref["zeta"])
+        out = solver.solve(Vd, Ne, 0.2, bounds=(chi, zeta))
+        torch.cuda.synchronize()
+        matol = FP64_MOM if prec == SQ_FP64 else 5e-5
+        np.testing.assert_allclose(out["moments"].cpu().numpy(), ref["moments"], rtol=0, atol=matol)
+        assert _rel2(out["rho"].cpu().numpy(), ref["rho"]) < rtol
+        gb = solver.bounds(Vd, 20, 0.01)
+        np.testing.assert_allclose(gb[0].cpu().numpy(), ref["chi"], rtol=FP64_BOUNDS if prec == SQ_FP64 else 1e-5)
+        solver.close()
+
+
+def test_errors_are_reported_not_faulted():
+    s = synth.make_system("al4_16")
+    wl = s.wl
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    V = _dev(s.V)
+    # a host tensor is rejected before any launch
+    with pytest.raises(TypeError):
+        solver.compute_moments(torch.from_numpy(s.V.ravel()))
+    # raw host pointer through the C ABI: SQ_EINVAL, no fault
+    import ctypes as C
+    host = np.zeros(wl.n_nodes)
+    rc = sq.load().sq_moments(C.c_void_p(solver.ctx), C.c_void_p(host.ctypes.data), C.c_void_p(solver.chi.data_ptr()),
+                              C.c_void_p(solver.zeta.data_ptr()), C.c_void_p(solver.moments.data_ptr()))
+    assert rc == sq.SQ_EINVAL
+    # bounds that do not enclose the spectrum: moments leave [-1, 1] -> SQ_EBOUNDS
+    chi = torch.full((wl.n_nodes,), 20.0, dtype=torch.float64, device=DEV)
+    zeta = torch.full((wl.n_nodes,), 5.0, dtype=torch.float64, device=DEV)
+    solver.compute_moments(V, chi, zeta)
+    with pytest.raises(SQError) as e:
+        solver.fermi_level(wl.n_electrons, wl.kT, chi, zeta)
+    assert e.value.code == sq.SQ_EBOUNDS
+    # the context stays usable afterwards
+    out = solver.solve(V, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)
+    assert abs(out["n_elec"] - wl.n_electrons) < 1e-8
+    # electron count outside (0, 2 N_d)
+    with pytest.raises(SQError) as e:
+        solver.fermi_level(2.0 * wl.n_nodes + 1, wl.kT)
+    assert e.value.code == sq.SQ_EINVAL
+    solver.close()
+
+
+def test_deterministic_repeat():
+    s = synth.make_system("al4_16")
+    wl = s.wl
+    a = _run(s, SQ_FP32)
+    b = _run(s, SQ_FP32)
+    assert np.array_equal(a["moments"], b["moments"])
+    assert np.array_equal(a["rho"], b["rho"]) and a["mu"] == b["mu"]
