@@ -17,7 +17,7 @@ __all__ = ["sq", "SQSolver", "SQ_FP32", "SQ_FP64", "SQError", "build"]
 
 
 def build(force: bool = False) -> str:
-    from .build import build as _build
+    from .builder import build as _build
     return _build(force=force)
 
 

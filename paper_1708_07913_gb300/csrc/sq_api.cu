@@ -106,8 +106,10 @@ int setup_projectors(sq_ctx* c, const double* xyz)
             at[I].lo[a] = lo;
             at[I].len[a] = hi - lo + 1;
             if (at[I].len[a] > NL_BOX) return SQ_EUNSUPPORTED;
+            c->lb = std::max(c->lb, at[I].len[a]);
         }
     }
+    if (c->lb < 1) c->lb = 1;
     for (int a = 0; a < 3; ++a) c->ntile[a] = (n[a] + TILE - 1) / TILE;
     const long long ntiles = (long long)c->ntile[0] * c->ntile[1] * c->ntile[2];
     // (tile, atom, box start) records; tiles meet a box iff the union of
@@ -144,9 +146,9 @@ int setup_projectors(sq_ctx* c, const double* xyz)
     int rc;
     size_t tsz = c->precision == SQ_FP32 ? sizeof(float) : sizeof(double);
     if ((rc = dev_alloc(&c->d_atoms, sizeof(AtomTab) * at.size()))) return rc;
-    if ((rc = dev_alloc(&c->d_G, tsz * 3 * NL_BOX * at.size()))) return rc;
-    if ((rc = dev_alloc(&c->d_DG, tsz * 3 * NL_BOX * at.size()))) return rc;
-    if ((rc = dev_alloc(&c->d_ivl, (size_t)NL_BOX * NL_BOX * 2 * at.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_G, tsz * 3 * c->lb * at.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_DG, tsz * 3 * c->lb * at.size()))) return rc;
+    if ((rc = dev_alloc(&c->d_ivl, (size_t)c->lb * c->lb * 2 * at.size()))) return rc;
     if ((rc = dev_alloc(&c->d_tile_start, sizeof(int) * start.size()))) return rc;
     if ((rc = dev_alloc(&c->d_tile_cand, sizeof(int4) * std::max<size_t>(cand.size(), 1)))) return rc;
     double* d_R = nullptr;
@@ -169,12 +171,14 @@ RegionArgs<T> region_args(sq_ctx* c)
     RegionArgs<T> a;
     memset(&a, 0, sizeof(a));
     a.g = c->g;
+    for (int d = 0; d <= FD_NO; ++d) a.wd[d] = (T)(-0.5 * c->g.w[d]);
     a.Vp = (const T*)c->Vp;
     a.nl.n_atoms = (c->has_s || c->has_p) ? c->n_atoms : 0;
     a.nl.atoms = c->d_atoms;
     a.nl.G = (const T*)c->d_G;
     a.nl.DG = (const T*)c->d_DG;
     a.nl.ivl = c->d_ivl;
+    a.nl.lb = c->lb;
     a.nl.tile_start = c->d_tile_start;
     a.nl.tile_cand = c->d_tile_cand;
     for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];

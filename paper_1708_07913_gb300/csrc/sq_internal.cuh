@@ -25,7 +25,7 @@ constexpr int MAX_M = 15;            // region side 2m+1 <= 31
 constexpr int NL_BOX = 32;           // max projector box length per axis (points)
 constexpr int TILE = 8;              // node tile edge for projector candidate lists
 constexpr int MAX_CAND = 512;        // projector candidates per node
-constexpr int ENTRIES_PER_ROW = 32;  // average row-entry capacity per region row
+constexpr int ENTRIES_PER_ROW = 16;  // average row-entry capacity per region row (about 7-8 are used)
 constexpr int MAX_NPL = 512;
 
 // Error bits latched on the device (combined into one sq_status on the host).
@@ -42,9 +42,10 @@ template <typename T>
 struct NLParams {
     int n_atoms;                     // 0 = local only
     const AtomTab* atoms;
-    const T* G;                      // [atom][3][NL_BOX]
-    const T* DG;                     // [atom][3][NL_BOX]
-    const uint8_t* ivl;              // [atom][NL_BOX][NL_BOX][2]  (xlo, xhi) box-relative, empty: xlo > xhi
+    int lb;                          // table stride: longest projector box edge (points, <= NL_BOX)
+    const T* G;                      // [atom][3][lb]
+    const T* DG;                     // [atom][3][lb]
+    const uint8_t* ivl;              // [atom][lb][lb][2]  (xlo, xhi) box-relative, empty: xlo > xhi
     const int* tile_start;           // [ntiles+1]
     const int4* tile_cand;           // (atom, box start x, y, z) unwrapped
     int ntile[3];
@@ -53,13 +54,26 @@ struct NLParams {
 };
 
 // Per-CTA scratch layout (device, one slice per resident CTA).
+// Projector entries are (candidate, region row) pairs with a non-empty clipped
+// support interval; they are kept twice: by row (candidates ascending) for the
+// update fused into the stencil sweep, and by candidate (rows ascending) for
+// the inner products.
+//   row-ordered meta:        c | xlo << 10 | xhi << 15
+//   candidate-ordered meta:  r | xlo << 10 | xhi << 15      (r = y + S z)
+//   factors f = (G_y G_z, DG_y G_z, G_y DG_z, 0) of the entry's row
 template <typename T>
 struct CtaScratch {
-    T* buf;                          // S^3 second vector
+    T* buf;                          // S^3 second vector (when not in shared memory)
     int4* cand;                      // MAX_CAND candidates (atom, bx, by, bz) region-relative
-    T* P;                            // MAX_CAND*4 projector dots
+    T* P;                            // MAX_CAND*4 projector inner products (S, X, Y, Z)
+    T* TX;                           // MAX_CAND*S*2: (G_x, DG_x) of candidate c at region column x (0 outside box)
+    uint32_t* ent_meta;              // cap, row-ordered
+    T* ent_f;                        // cap*4, row-ordered
+    uint32_t* cent_meta;             // cap, candidate-ordered
+    T* cent_f;                       // cap*4, candidate-ordered
     int* row_start;                  // S^2 + 1
-    uint32_t* entries;               // S^2 * ENTRIES_PER_ROW (cand | xlo<<16 | xhi<<24)
+    int* row_fill;                   // S^2
+    int* cand_start;                 // MAX_CAND + 1
 };
 
 struct GridParams {
@@ -90,6 +104,7 @@ struct sq_ctx {
     void* d_G;
     void* d_DG;
     uint8_t* d_ivl;
+    int lb;
     int* d_tile_start;
     int4* d_tile_cand;
     int ntile[3];

@@ -56,25 +56,25 @@ int launch_build_vpad(sq_ctx* ctx, const double* V)
 // ------------------------------------------------------------------------
 template <typename T>
 __global__ void proj_table_kernel(const double* __restrict__ R, const AtomTab* __restrict__ at, int n_atoms,
-                                  double h, double rc, double rnl2, T* G, T* DG, uint8_t* ivl)
+                                  int lb, double h, double rc, double rnl2, T* G, T* DG, uint8_t* ivl)
 {
     const int atom = blockIdx.x;
     if (atom >= n_atoms) return;
     const AtomTab A = at[atom];
     const double two_rc2 = 2.0 * rc * rc;
-    for (int t = threadIdx.x; t < 3 * NL_BOX; t += blockDim.x) {
-        int ax = t / NL_BOX, i = t % NL_BOX;
+    for (int t = threadIdx.x; t < 3 * lb; t += blockDim.x) {
+        int ax = t / lb, i = t % lb;
         double g = 0.0, dg = 0.0;
         if (i < A.len[ax]) {
             double d = __dadd_rn(__dmul_rn((double)(A.lo[ax] + i), h), -R[3 * atom + ax]);
             g = exp(-__dmul_rn(d, d) / two_rc2);
             dg = d * g;
         }
-        G[((size_t)atom * 3 + ax) * NL_BOX + i] = (T)g;
-        DG[((size_t)atom * 3 + ax) * NL_BOX + i] = (T)dg;
+        G[((size_t)atom * 3 + ax) * lb + i] = (T)g;
+        DG[((size_t)atom * 3 + ax) * lb + i] = (T)dg;
     }
-    for (int t = threadIdx.x; t < NL_BOX * NL_BOX; t += blockDim.x) {
-        int jj = t / NL_BOX, kk = t % NL_BOX;
+    for (int t = threadIdx.x; t < lb * lb; t += blockDim.x) {
+        int jj = t / lb, kk = t % lb;
         int xlo = 1, xhi = 0;
         if (jj < A.len[1] && kk < A.len[2]) {
             double dy = __dadd_rn(__dmul_rn((double)(A.lo[1] + jj), h), -R[3 * atom + 1]);
@@ -90,8 +90,8 @@ __global__ void proj_table_kernel(const double* __restrict__ R, const AtomTab* _
             }
             if (first >= 0) { xlo = first; xhi = last; }
         }
-        ivl[(((size_t)atom * NL_BOX + jj) * NL_BOX + kk) * 2 + 0] = (uint8_t)xlo;
-        ivl[(((size_t)atom * NL_BOX + jj) * NL_BOX + kk) * 2 + 1] = (uint8_t)xhi;
+        ivl[(((size_t)atom * lb + jj) * lb + kk) * 2 + 0] = (uint8_t)xlo;
+        ivl[(((size_t)atom * lb + jj) * lb + kk) * 2 + 1] = (uint8_t)xhi;
     }
 }
 
@@ -100,11 +100,11 @@ int launch_proj_tables(sq_ctx* ctx, const double* d_R)
     double rnl2 = ctx->rnl * ctx->rnl;
     if (ctx->precision == SQ_FP32)
         proj_table_kernel<float><<<ctx->n_atoms, 256, 0, ctx->stream>>>(
-            d_R, ctx->d_atoms, ctx->n_atoms, ctx->g.h, ctx->rc, rnl2, (float*)ctx->d_G, (float*)ctx->d_DG,
+            d_R, ctx->d_atoms, ctx->n_atoms, ctx->lb, ctx->g.h, ctx->rc, rnl2, (float*)ctx->d_G, (float*)ctx->d_DG,
             ctx->d_ivl);
     else
         proj_table_kernel<double><<<ctx->n_atoms, 256, 0, ctx->stream>>>(
-            d_R, ctx->d_atoms, ctx->n_atoms, ctx->g.h, ctx->rc, rnl2, (double*)ctx->d_G, (double*)ctx->d_DG,
+            d_R, ctx->d_atoms, ctx->n_atoms, ctx->lb, ctx->g.h, ctx->rc, rnl2, (double*)ctx->d_G, (double*)ctx->d_DG,
             ctx->d_ivl);
     ctx->launches++;
     return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;
@@ -360,8 +360,11 @@ __global__ void fermi_count_kernel(const double* __restrict__ W, const double* _
         const double* w = W + q * K;
         double s = 0.0;
         for (int k = 0; k < K; ++k) {
-            double E = c + z * xk[k];
-            s += w[k] / (1.0 + exp((E - mu) / kT));
+            double t = (c + z * xk[k] - mu) / kT;
+            // beyond |t| = 40 the Fermi factor is 1.0 exactly in FP64 (t < -40)
+            // or below 4.3e-18 (t > 40, dropped: < 1e-16 of any count here)
+            if (t > 40.0) continue;
+            s += (t < -40.0) ? w[k] : w[k] / (1.0 + exp(t));
         }
         acc[0] += 2.0 * s;
     }
@@ -441,9 +444,15 @@ __global__ void density_kernel(const double* __restrict__ W, const double* __res
         for (int k = 0; k < K; ++k) {
             double E = c + z * xk[k];
             double t = (E - mu) / kT;
+            if (t > 40.0) continue;                    // g < 4.3e-18: no density, energy or entropy
+            double wk = w[k];
+            if (t < -40.0) {                           // g == 1.0 exactly in FP64, entropy term 0
+                r += wk;
+                eb += 2.0 * wk * E;
+                continue;
+            }
             double g = 1.0 / (1.0 + exp(t));
             double gm = 1.0 / (1.0 + exp(-t));
-            double wk = w[k];
             r += wk * g;
             eb += 2.0 * wk * E * g;
             double sf = 0.0;

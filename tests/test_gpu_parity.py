@@ -158,7 +158,8 @@ def test_edge_geometries_fp64_and_fp32(shape, r_cut, npl, nonlocal_):
     osys = oracle.OracleSystem(V, h, m, pos, pt)
     nodes = np.arange(n1 * n2 * n3)
     Ne = 0.3 * nodes.size
-    ref = oracle.solve(osys, npl, 0.2, Ne, 20, 0.01)
+    ref = oracle.solve(osys, npl, 0.2, Ne, 40, 0.01)
+    assert np.abs(ref["moments"]).max() <= 1 + 1e-9          # the bounds enclose every spectrum
     for prec, rtol in ((SQ_FP64, FP64_RHO), (SQ_FP32, 1e-4)):
         solver = SQSolver(shape, h, r_cut, npl, prec, pos, pt, device=DEV)
         Vd = _dev(V)
@@ -168,7 +169,7 @@ def test_edge_geometries_fp64_and_fp32(shape, r_cut, npl, nonlocal_):
         matol = FP64_MOM if prec == SQ_FP64 else 5e-5
         np.testing.assert_allclose(out["moments"].cpu().numpy(), ref["moments"], rtol=0, atol=matol)
         assert _rel2(out["rho"].cpu().numpy(), ref["rho"]) < rtol
-        gb = solver.bounds(Vd, 20, 0.01)
+        gb = solver.bounds(Vd, 40, 0.01)
         np.testing.assert_allclose(gb[0].cpu().numpy(), ref["chi"], rtol=FP64_BOUNDS if prec == SQ_FP64 else 1e-5)
         solver.close()
 
@@ -211,3 +212,22 @@ def test_deterministic_repeat():
     b = _run(s, SQ_FP32)
     assert np.array_equal(a["moments"], b["moments"])
     assert np.array_equal(a["rho"], b["rho"]) and a["mu"] == b["mu"]
+
+
+def test_unconverged_bounds_are_reported():
+    """Too few Lanczos steps on a rough potential: the widened Ritz interval
+    misses part of the spectrum, the oracle's own moments leave [-1, 1], and
+    the GPU path reports SQ_EBOUNDS instead of returning them."""
+    n1 = n2 = n3 = 10
+    pos = synth.fcc_positions(1, 0.3, 77)
+    h = synth.LATTICE_A / n1
+    rng = np.random.default_rng(5)
+    V = -1.5 + 0.5 * rng.standard_normal((n3, n2, n1))
+    pt = synth.projector_types(True)
+    ref = oracle.solve(oracle.OracleSystem(V, h, 3, pos, pt), 24, 0.2, 300.0, 20, 0.01)
+    assert np.abs(ref["moments"]).max() > 1.5
+    solver = SQSolver((n1, n2, n3), h, 3.0, 24, SQ_FP64, pos, pt, device=DEV)
+    with pytest.raises(SQError) as e:
+        solver.solve(_dev(V), 300.0, 0.2, n_lanczos=20, margin=0.01)
+    assert e.value.code == sq.SQ_EBOUNDS
+    solver.close()
