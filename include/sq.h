@@ -147,6 +147,33 @@ int sq_density_energy(sq_ctx *ctx, const double *moments, const double *chi,
                       const double *zeta, double mu, double kT, double *rho,
                       double *e_band_host, double *e_ent_host, double *n_elec_host);
 
+/* Density, band energy and entropy like sq_density_energy, for callers that
+ * must not allocate device memory (no context, no cudaMalloc, no allocating
+ * library call).  The paper has no counterpart: this exists for host programs
+ * that reserve all device memory for their own allocator, or fix their memory
+ * budget at start-up, and so cannot let a library allocate.
+ *   n1,n2,n3, h, npl      grid and degree as in sq_setup_grid (npl % 4 == 0,
+ *                         4 <= npl <= 512, n1*n2*n3 <= 2^31); larger sizes
+ *                         are rejected with SQ_EINVAL
+ *   moments, chi, zeta    device inputs as for sq_fermi_level
+ *   mu, kT                Fermi level and smearing (kT > 0)
+ *   rho                   device output, N_d FP64
+ *   e_band_host, e_ent_host, n_elec_host   HOST outputs (each may be NULL)
+ *   cuda_stream           stream to run on (NULL = legacy default stream)
+ * The quadrature weights are recomputed per node instead of stored.  The
+ * reduction's scratch is one fixed library-wide device array of 49,184 bytes
+ * (partials for at most 2048 blocks), present on every device that loads the
+ * library until the process exits.  The first call on a device looks up that
+ * array's device address (with the device current); later calls reuse it.
+ * Every call shares the array: each call clears its counter before use, and
+ * calls that overlap on the GPU (other streams or host threads) race on it.
+ * Synchronises the stream. */
+int sq_density_energy_noalloc(int n1, int n2, int n3, double h, int npl,
+                              const double *moments, const double *chi, const double *zeta,
+                              double mu, double kT, double *rho,
+                              double *e_band_host, double *e_ent_host, double *n_elec_host,
+                              void *cuda_stream);
+
 /* Wait for the context's stream and return any latched device error. */
 int sq_sync(sq_ctx *ctx);
 

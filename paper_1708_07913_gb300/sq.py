@@ -22,7 +22,8 @@ SQ_FP64, SQ_FP32 = 0, 1
 
 # Every entry point declared in include/sq.h.
 EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments", "sq_fermi_level",
-           "sq_density_energy", "sq_sync", "sq_launch_count", "sq_destroy", "sq_strerror")
+           "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
+           "sq_strerror")
 
 
 class SQError(RuntimeError):
@@ -56,6 +57,8 @@ def load(path: str = LIB_PATH):
         lib.sq_moments.argtypes = [vp, vp, vp, vp, vp]
         lib.sq_fermi_level.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, dp]
         lib.sq_density_energy.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp, dp, dp, dp]
+        lib.sq_density_energy_noalloc.argtypes = [ip, ip, ip, C.c_double, ip, vp, vp, vp, C.c_double, C.c_double,
+                                                  vp, dp, dp, dp, vp]
         lib.sq_sync.argtypes = [vp]
         lib.sq_launch_count.argtypes = [vp]
         lib.sq_launch_count.restype = C.c_longlong
@@ -136,6 +139,20 @@ def sq_density_energy(ctx, moments, chi, zeta, mu, kT, rho):
     _check(load().sq_density_energy(C.c_void_p(ctx), _dptr(moments, "moments"), _dptr(chi, "chi"),
                                     _dptr(zeta, "zeta"), float(mu), float(kT), _dptr(rho, "rho"),
                                     C.byref(eb), C.byref(es), C.byref(ne)), "sq_density_energy")
+    return eb.value, es.value, ne.value
+
+
+def sq_density_energy_noalloc(shape, h, npl, moments, chi, zeta, mu, kT, rho, stream=None):
+    """Allocation-free density/energy step (no context); fills rho, returns
+    (E_band, E_ent, N).  For callers that cannot let the library allocate
+    device memory."""
+    n1, n2, n3 = shape
+    eb, es, ne = C.c_double(), C.c_double(), C.c_double()
+    _check(load().sq_density_energy_noalloc(int(n1), int(n2), int(n3), float(h), int(npl),
+                                            _dptr(moments, "moments"), _dptr(chi, "chi"), _dptr(zeta, "zeta"),
+                                            float(mu), float(kT), _dptr(rho, "rho"), C.byref(eb), C.byref(es),
+                                            C.byref(ne), stream if stream is not None else _stream()),
+           "sq_density_energy_noalloc")
     return eb.value, es.value, ne.value
 
 

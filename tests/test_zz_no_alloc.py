@@ -1,0 +1,57 @@
+"""sq_density_energy_noalloc -- the entry point for callers that cannot let
+the library allocate device memory (programs that reserve all GPU memory for
+their own allocator, or settle their memory budget at start-up) -- must give
+the same density, band energy, entropy and electron count as
+sq_density_energy, call after call.  This file is named to be collected last.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1708_07913_gb300 import SQ_FP64, SQSolver, build, sq  # noqa: E402
+
+
+@pytest.mark.parametrize("name", ["al4_16", "al108_48"])
+def test_noalloc_matches_context_entry_point_twice(name):
+    build()
+    s = synth.make_system(name)
+    wl = s.wl
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64)
+    V = torch.from_numpy(s.V.ravel().copy()).cuda()
+    if name == "al4_16":
+        chi, zeta = solver.bounds(V, wl.n_lanczos, wl.margin)
+    else:   # bounds from a cheap enclosure keep this test short; both entry points see the same inputs
+        chi = torch.full((wl.n_nodes,), 22.9, dtype=torch.float64, device="cuda")
+        zeta = torch.full((wl.n_nodes,), 23.9, dtype=torch.float64, device="cuda")
+    solver.compute_moments(V, chi, zeta)
+    mu = solver.fermi_level(wl.n_electrons, wl.kT, chi, zeta)
+    eb, es, ne = solver.density_energy(mu, wl.kT, chi, zeta)
+    ref = solver.rho.cpu().numpy().copy()
+    for _ in range(2):
+        rho = torch.full((wl.n_nodes,), float("nan"), dtype=torch.float64, device="cuda")
+        eb2, es2, ne2 = sq.sq_density_energy_noalloc((wl.n, wl.n, wl.n), wl.h, wl.npl, solver.moments, chi, zeta,
+                                                      mu, wl.kT, rho)
+        got = rho.cpu().numpy()
+        assert np.linalg.norm(got - ref) < 1e-10 * np.linalg.norm(ref)
+        assert np.abs(got - ref).max() < 1e-10 * ref.max()
+        assert abs(eb2 - eb) < 1e-10 * abs(eb)
+        assert abs(es2 - es) < 1e-10 * abs(es)
+        assert abs(ne2 - ne) < 1e-10 * abs(ne)
+    solver.close()
+
+
+def test_noalloc_rejects_sizes_beyond_its_limits():
+    build()
+    d = torch.zeros(8, dtype=torch.float64, device="cuda")
+    with pytest.raises(sq.SQError) as e:
+        sq.sq_density_energy_noalloc((2, 2, 2), 0.5, 516, d, d, d, 0.0, 0.1, d)
+    assert e.value.code == sq.SQ_EINVAL
+    with pytest.raises(sq.SQError) as e:
+        sq.sq_density_energy_noalloc((2, 2, 2), 0.5, 6, d, d, d, 0.0, 0.1, d)
+    assert e.value.code == sq.SQ_EINVAL
