@@ -13,10 +13,10 @@
 #include "sq_region.cuh"
 
 namespace sq {
-int region_config_f32(int m, int which, int* bps, size_t* smem);
-int region_config_f64(int m, int which, int* bps, size_t* smem);
-int region_launch_f32(int m, int which, const RegionArgs<float>& a, int blocks, cudaStream_t st);
-int region_launch_f64(int m, int which, const RegionArgs<double>& a, int blocks, cudaStream_t st);
+int region_config_f32(int m, int which, size_t extra, int* bps, size_t* smem);
+int region_config_f64(int m, int which, size_t extra, int* bps, size_t* smem);
+int region_launch_f32(int m, int which, const RegionArgs<float>& a, size_t extra, int blocks, cudaStream_t st);
+int region_launch_f64(int m, int which, const RegionArgs<double>& a, size_t extra, int blocks, cudaStream_t st);
 }  // namespace sq
 
 using namespace sq;
@@ -143,6 +143,59 @@ int setup_projectors(sq_ctx* c, const double* xyz)
     std::vector<int> fill(start.begin(), start.end() - 1);
     for (auto& r : recs) cand[fill[r.tile]++] = make_int4(r.atom, r.bx, r.by, r.bz);   // stable: atom order
 
+    // Largest number of candidates of any node: per tile, a 3-D difference
+    // array over the tile's node offsets counts, for every node, the boxes
+    // that meet its region (node i meets box [b0, b1] iff b0 - m <= i <= b1 + m).
+    c->ccap = 0;
+    {
+        const int W = TILE + 1;
+        std::vector<int> D(W * W * W);
+        for (int tz = 0; tz < c->ntile[2]; ++tz)
+            for (int ty = 0; ty < c->ntile[1]; ++ty)
+                for (int tx = 0; tx < c->ntile[0]; ++tx) {
+                    long long tile = tx + (long long)c->ntile[0] * (ty + (long long)c->ntile[1] * tz);
+                    std::fill(D.begin(), D.end(), 0);
+                    const int t0[3] = {tx * TILE, ty * TILE, tz * TILE};
+                    for (int k = start[tile]; k < start[tile + 1]; ++k) {
+                        const int4 cd = cand[k];
+                        const int b0[3] = {cd.y, cd.z, cd.w};
+                        int lo[3], hi[3];
+                        bool empty = false;
+                        for (int a = 0; a < 3; ++a) {
+                            int l = std::max(b0[a] - m, t0[a]);
+                            int h = std::min(b0[a] + at[cd.x].len[a] - 1 + m, std::min(t0[a] + TILE, n[a]) - 1);
+                            lo[a] = l - t0[a];
+                            hi[a] = h - t0[a];
+                            if (h < l) empty = true;
+                        }
+                        if (empty) continue;
+                        auto add = [&](int x, int y, int z, int v) { D[x + W * (y + W * z)] += v; };
+                        add(lo[0], lo[1], lo[2], 1);
+                        add(hi[0] + 1, lo[1], lo[2], -1);
+                        add(lo[0], hi[1] + 1, lo[2], -1);
+                        add(lo[0], lo[1], hi[2] + 1, -1);
+                        add(hi[0] + 1, hi[1] + 1, lo[2], 1);
+                        add(hi[0] + 1, lo[1], hi[2] + 1, 1);
+                        add(lo[0], hi[1] + 1, hi[2] + 1, 1);
+                        add(hi[0] + 1, hi[1] + 1, hi[2] + 1, -1);
+                    }
+                    for (int z = 0; z < W; ++z)              // prefix sums along x, y, z
+                        for (int y = 0; y < W; ++y)
+                            for (int x = 1; x < W; ++x) D[x + W * (y + W * z)] += D[x - 1 + W * (y + W * z)];
+                    for (int z = 0; z < W; ++z)
+                        for (int y = 1; y < W; ++y)
+                            for (int x = 0; x < W; ++x) D[x + W * (y + W * z)] += D[x + W * (y - 1 + W * z)];
+                    for (int z = 1; z < W; ++z)
+                        for (int y = 0; y < W; ++y)
+                            for (int x = 0; x < W; ++x) D[x + W * (y + W * z)] += D[x + W * (y + W * (z - 1))];
+                    for (int z = 0; z < TILE; ++z)
+                        for (int y = 0; y < TILE; ++y)
+                            for (int x = 0; x < TILE; ++x) c->ccap = std::max(c->ccap, D[x + W * (y + W * z)]);
+                }
+    }
+    if (c->ccap > MAX_CAND) return SQ_ECAPACITY;
+    if (c->ccap < 1) c->ccap = 1;
+
     int rc;
     size_t tsz = c->precision == SQ_FP32 ? sizeof(float) : sizeof(double);
     if ((rc = dev_alloc(&c->d_atoms, sizeof(AtomTab) * at.size()))) return rc;
@@ -179,6 +232,8 @@ RegionArgs<T> region_args(sq_ctx* c)
     a.nl.DG = (const T*)c->d_DG;
     a.nl.ivl = c->d_ivl;
     a.nl.lb = c->lb;
+    a.nl.ccap = c->ccap;
+    a.nl.smem = c->nl_extra > 0;
     a.nl.tile_start = c->d_tile_start;
     a.nl.tile_cand = c->d_tile_cand;
     for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
@@ -195,12 +250,20 @@ RegionArgs<T> region_args(sq_ctx* c)
     return a;
 }
 
+// Dynamic shared memory beyond the region vectors: the moments kernel (which
+// = 0) keeps its per-node moment sums there; both keep the projector tables
+// there when they fit.
+size_t region_extra(const sq_ctx* c, int which)
+{
+    return (which == 0 ? mom_smem_bytes(c->npl) : 0) + c->nl_extra;
+}
+
 int region_blocks(sq_ctx* c, int which, int* blocks)
 {
     int bps = 0;
     size_t smem = 0;
-    int rc = c->precision == SQ_FP32 ? region_config_f32(c->g.m, which, &bps, &smem)
-                                     : region_config_f64(c->g.m, which, &bps, &smem);
+    int rc = c->precision == SQ_FP32 ? region_config_f32(c->g.m, which, region_extra(c, which), &bps, &smem)
+                                     : region_config_f64(c->g.m, which, region_extra(c, which), &bps, &smem);
     if (rc) return rc;
     long long b = (long long)bps * c->sm_count;
     if (b > c->g.Nd) b = c->g.Nd;
@@ -296,7 +359,14 @@ int sq_setup_grid(sq_ctx** out, int n1, int n2, int n3, double h, int fd_half_or
     } else {
         c->ntile[0] = c->ntile[1] = c->ntile[2] = 1;
     }
+    // projector tables of the candidates in shared memory when they fit next
+    // to the region vectors (both kernels must accept the size)
     int bm = 0, bl = 0;
+    c->nl_extra = 0;
+    if (c->n_atoms > 0) {
+        c->nl_extra = nl_smem_bytes(c->ccap, 2 * m + 1, tsz);
+        if (region_blocks(c, 0, &bm) != SQ_OK || region_blocks(c, 1, &bl) != SQ_OK) c->nl_extra = 0;
+    }
     if ((rcode = region_blocks(c, 0, &bm)) || (rcode = region_blocks(c, 1, &bl))) { free_ctx(c); return rcode; }
     c->grid_blocks = std::max(bm, bl);
     c->scratch_bytes_per_cta = scratch_layout(m, tsz).total;
@@ -353,11 +423,11 @@ int sq_spectral_bounds(sq_ctx* c, const double* V, double* chi, double* zeta, in
     if (c->precision == SQ_FP32) {
         RegionArgs<float> a = region_args<float>(c);
         a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
-        rc = region_launch_f32(c->g.m, 1, a, blocks, c->stream);
+        rc = region_launch_f32(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
     } else {
         RegionArgs<double> a = region_args<double>(c);
         a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
-        rc = region_launch_f64(c->g.m, 1, a, blocks, c->stream);
+        rc = region_launch_f64(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
     }
     c->launches++;
     if (rc) return rc;
@@ -376,11 +446,11 @@ int sq_moments(sq_ctx* c, const double* V, const double* chi, const double* zeta
     if (c->precision == SQ_FP32) {
         RegionArgs<float> a = region_args<float>(c);
         a.chi = chi; a.zeta = zeta; a.moments = moments;
-        rc = region_launch_f32(c->g.m, 0, a, blocks, c->stream);
+        rc = region_launch_f32(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
     } else {
         RegionArgs<double> a = region_args<double>(c);
         a.chi = chi; a.zeta = zeta; a.moments = moments;
-        rc = region_launch_f64(c->g.m, 0, a, blocks, c->stream);
+        rc = region_launch_f64(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
     }
     c->launches++;
     return rc;

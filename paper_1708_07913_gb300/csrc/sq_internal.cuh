@@ -25,8 +25,9 @@ constexpr int MAX_M = 15;            // region side 2m+1 <= 31
 constexpr int NL_BOX = 32;           // max projector box length per axis (points)
 constexpr int TILE = 8;              // node tile edge for projector candidate lists
 constexpr int MAX_CAND = 512;        // projector candidates per node
-constexpr int ENTRIES_PER_ROW = 16;  // average row-entry capacity per region row (about 7-8 are used)
+constexpr int ENTRIES_PER_ROW = 24;  // projector entries a region row may hold (FCC Al at h ~ 0.48: up to 14)
 constexpr int MAX_NPL = 512;
+constexpr int STAGE = 16;            // row entries staged per warp at a time in the projector update
 
 // Error bits latched on the device (combined into one sq_status on the host).
 constexpr unsigned ERR_BOUNDS = 1u;
@@ -49,31 +50,48 @@ struct NLParams {
     const int* tile_start;           // [ntiles+1]
     const int4* tile_cand;           // (atom, box start x, y, z) unwrapped
     int ntile[3];
+    int ccap;                        // most candidates any node has (exact, from the set-up)
+    int smem;                        // 1: the per-candidate tables live in shared memory after the region vectors
     T cs;                            // h^3 gamma_s A_s^2   (0 if no s channel)
     T cp;                            // h^3 gamma_p A_p^2   (0 if no p channel)
 };
 
-// Per-CTA scratch layout (device, one slice per resident CTA).
-// Projector entries are (candidate, region row) pairs with a non-empty clipped
-// support interval; they are kept twice: by row (candidates ascending) for the
-// update fused into the stencil sweep, and by candidate (rows ascending) for
-// the inner products.
-//   row-ordered meta:        c | xlo << 10 | xhi << 15
-//   candidate-ordered meta:  r | xlo << 10 | xhi << 15      (r = y + S z)
-//   factors f = (G_y G_z, DG_y G_z, G_y DG_z, 0) of the entry's row
+// Projector entry record: one (candidate, region row) pair whose clipped
+// support interval in x is non-empty, with the row's y/z Gaussian factors
+//   f0 = G_y G_z,  f1 = DG_y G_z,  f2 = G_y DG_z.
+// meta = key | xlo << 10 | xhi << 15, where key is the region row r = y + S z
+// in candidate order and the candidate index c in row order.  One 16-byte
+// load in FP32.
+template <typename T>
+struct __align__(16) EntRec {
+    uint32_t meta;
+    T f0, f1, f2;
+};
+static_assert(sizeof(EntRec<float>) == 16 && sizeof(EntRec<double>) == 32, "record sizes assumed by the scratch layout");
+
+// Per-CTA scratch (device, one slice per resident CTA).  The entries are kept
+// twice, both built once per node and read every step:
+//   by candidate (rows ascending within a candidate; candidate c owns
+//     cent[cand_start[c] .. cand_start[c+1])), cut into chunks of 32 entries
+//     (chunk_first[c] = first chunk of c) for the inner products;
+//   by row, ENTRIES_PER_ROW slots per region row (candidates ascending), for
+//     the update of the second vector.
+// Everything but the entry lists moves to shared memory when it fits
+// (NLParams::smem).
 template <typename T>
 struct CtaScratch {
     T* buf;                          // S^3 second vector (when not in shared memory)
-    int4* cand;                      // MAX_CAND candidates (atom, bx, by, bz) region-relative
-    T* P;                            // MAX_CAND*4 projector inner products (S, X, Y, Z)
-    T* TX;                           // MAX_CAND*S*2: (G_x, DG_x) of candidate c at region column x (0 outside box)
-    uint32_t* ent_meta;              // cap, row-ordered
-    T* ent_f;                        // cap*4, row-ordered
-    uint32_t* cent_meta;             // cap, candidate-ordered
-    T* cent_f;                       // cap*4, candidate-ordered
-    int* row_start;                  // S^2 + 1
-    int* row_fill;                   // S^2
-    int* cand_start;                 // MAX_CAND + 1
+    int4* cand;                      // candidates (atom, bx, by, bz): box start relative to the region
+    int* clen;                       // candidate box lengths len_x | len_y << 8 | len_z << 16
+    T* P;                            // 4 per candidate: projector inner products (S, X, Y, Z)
+    T* TX;                           // S*2 per candidate: (G_x, DG_x) at region column x (0 outside its box)
+    T* seg;                          // 4 per (candidate + warp): partial inner products of one warp
+    EntRec<T>* cent;                 // candidate-ordered entries
+    EntRec<T>* rec;                  // row-ordered entries, ENTRIES_PER_ROW per row
+    EntRec<T>* stage;                // STAGE per warp: (meta, b0, b1) of the entries of the row in hand
+    int* cand_start;                 // ncand + 1
+    int* chunk_first;                // ncand + 1
+    uint8_t* row_n;                  // S^2: entries of each row
 };
 
 struct GridParams {
@@ -105,6 +123,8 @@ struct sq_ctx {
     void* d_DG;
     uint8_t* d_ivl;
     int lb;
+    int ccap;                        // most projector candidates of any node
+    size_t nl_extra;                 // shared-memory bytes of the candidate tables (0: in global scratch)
     int* d_tile_start;
     int4* d_tile_cand;
     int ntile[3];

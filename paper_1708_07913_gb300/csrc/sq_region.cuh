@@ -71,31 +71,72 @@ constexpr int region_min_blocks()
     return b < 1 ? 1 : b;
 }
 
+// Dynamic shared memory of the region vectors.
+template <typename T, int M>
+__host__ __device__ constexpr size_t region_smem()
+{
+    return (fits_double_buffer<T, M>() ? 2 : 1) * (size_t)Geo<M>::ELEMS * sizeof(T);
+}
+
 // Per-CTA scratch carving (identical on host and device).
 struct ScratchLayout {
-    size_t buf, cand, P, TX, ent_meta, ent_f, cent_meta, cent_f, row_start, row_fill, cand_start, total;
+    size_t buf, cand, clen, P, TX, seg, cent, rec, stage, cand_start, chunk_first, row_n, total;
 };
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline size_t rec_size(size_t tsize) { return tsize == 4 ? 16 : 32; }   // sizeof(EntRec<T>)
 __host__ __device__ inline ScratchLayout scratch_layout(int m, size_t tsize)
 {
     int S = 2 * m + 1;
     ScratchLayout L;
     size_t off = 0;
     const size_t cap = (size_t)S * S * ENTRIES_PER_ROW;
-    L.buf = off;        off = align256(off + (size_t)S * S * S * tsize);
-    L.cand = off;       off = align256(off + (size_t)MAX_CAND * sizeof(int4));
-    L.P = off;          off = align256(off + (size_t)MAX_CAND * 4 * tsize);
-    L.TX = off;         off = align256(off + (size_t)MAX_CAND * S * 2 * tsize);
-    L.ent_meta = off;   off = align256(off + cap * sizeof(uint32_t));
-    L.ent_f = off;      off = align256(off + cap * 4 * tsize);
-    L.cent_meta = off;  off = align256(off + cap * sizeof(uint32_t));
-    L.cent_f = off;     off = align256(off + cap * 4 * tsize);
-    L.row_start = off;  off = align256(off + (size_t)(S * S + 1) * sizeof(int));
-    L.row_fill = off;   off = align256(off + (size_t)S * S * sizeof(int));
-    L.cand_start = off; off = align256(off + (size_t)(MAX_CAND + 1) * sizeof(int));
+    L.buf = off;         off = align256(off + (size_t)S * S * S * tsize);
+    L.cand = off;        off = align256(off + (size_t)MAX_CAND * sizeof(int4));
+    L.clen = off;        off = align256(off + (size_t)MAX_CAND * sizeof(int));
+    L.P = off;           off = align256(off + (size_t)MAX_CAND * 4 * tsize);
+    L.TX = off;          off = align256(off + (size_t)MAX_CAND * S * 2 * tsize);
+    L.seg = off;         off = align256(off + (size_t)(MAX_CAND + 32) * 4 * tsize);
+    L.cent = off;        off = align256(off + cap * rec_size(tsize));
+    L.rec = off;         off = align256(off + cap * rec_size(tsize));
+    L.stage = off;       off = align256(off + (size_t)32 * STAGE * rec_size(tsize));
+    L.cand_start = off;  off = align256(off + (size_t)(MAX_CAND + 1) * sizeof(int));
+    L.chunk_first = off; off = align256(off + (size_t)(MAX_CAND + 1) * sizeof(int));
+    L.row_n = off;       off = align256(off + (size_t)S * S);
     L.total = off;
     return L;
 }
+
+// Shared-memory placement of the per-candidate tables for ccap candidates
+// (offsets from a 16-byte aligned base; total includes 16 bytes of slack for
+// aligning that base).
+struct NLSmem {
+    size_t cand, P, TX, seg, stage, clen, cand_start, chunk_first, row_n, total;
+};
+__host__ __device__ inline NLSmem nl_smem_layout(int ccap, int S, size_t tsize)
+{
+    NLSmem L;
+    size_t o = 0;
+    L.cand = o;        o = align16(o + (size_t)ccap * sizeof(int4));
+    L.P = o;           o = align16(o + (size_t)ccap * 4 * tsize);
+    L.TX = o;          o = align16(o + (size_t)ccap * 2 * S * tsize);
+    L.seg = o;         o = align16(o + (size_t)(ccap + 32) * 4 * tsize);
+    L.stage = o;       o = align16(o + (size_t)S * STAGE * rec_size(tsize));
+    L.clen = o;        o = align16(o + (size_t)ccap * sizeof(int));
+    L.cand_start = o;  o = align16(o + (size_t)(ccap + 1) * sizeof(int));
+    L.chunk_first = o; o = align16(o + (size_t)(ccap + 1) * sizeof(int));
+    L.row_n = o;       o = align16(o + (size_t)S * S);
+    L.total = o + 16;
+    return L;
+}
+__host__ __device__ inline size_t nl_smem_bytes(int ccap, int S, size_t tsize)
+{
+    return nl_smem_layout(ccap, S, tsize).total;
+}
+
+// Per-node moment scratch of the moments kernel in dynamic shared memory:
+// rho^i (centre values) and the two product sums, npl/2 + 2 each.
+__host__ __device__ inline size_t mom_smem_bytes(int npl) { return 16 + (size_t)3 * (npl / 2 + 2) * sizeof(double); }
 
 template <typename T>
 struct RegionArgs {
@@ -128,16 +169,68 @@ __device__ inline CtaScratch<T> cta_scratch(const RegionArgs<T>& a, int m)
     CtaScratch<T> s;
     s.buf = reinterpret_cast<T*>(base + L.buf);
     s.cand = reinterpret_cast<int4*>(base + L.cand);
+    s.clen = reinterpret_cast<int*>(base + L.clen);
     s.P = reinterpret_cast<T*>(base + L.P);
     s.TX = reinterpret_cast<T*>(base + L.TX);
-    s.ent_meta = reinterpret_cast<uint32_t*>(base + L.ent_meta);
-    s.ent_f = reinterpret_cast<T*>(base + L.ent_f);
-    s.cent_meta = reinterpret_cast<uint32_t*>(base + L.cent_meta);
-    s.cent_f = reinterpret_cast<T*>(base + L.cent_f);
-    s.row_start = reinterpret_cast<int*>(base + L.row_start);
-    s.row_fill = reinterpret_cast<int*>(base + L.row_fill);
+    s.seg = reinterpret_cast<T*>(base + L.seg);
+    s.cent = reinterpret_cast<EntRec<T>*>(base + L.cent);
+    s.rec = reinterpret_cast<EntRec<T>*>(base + L.rec);
+    s.stage = reinterpret_cast<EntRec<T>*>(base + L.stage);
     s.cand_start = reinterpret_cast<int*>(base + L.cand_start);
+    s.chunk_first = reinterpret_cast<int*>(base + L.chunk_first);
+    s.row_n = reinterpret_cast<uint8_t*>(base + L.row_n);
     return s;
+}
+
+// Move the per-candidate tables into shared memory at p (at least
+// nl_smem_bytes(ccap, S, sizeof(T)) bytes available).
+template <typename T>
+__device__ inline void nl_tables_in_smem(CtaScratch<T>& s, void* p_, int ccap, int S)
+{
+    char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p_) + 15) & ~uintptr_t(15));
+    const NLSmem L = nl_smem_layout(ccap, S, sizeof(T));
+    s.cand = reinterpret_cast<int4*>(p + L.cand);
+    s.P = reinterpret_cast<T*>(p + L.P);
+    s.TX = reinterpret_cast<T*>(p + L.TX);
+    s.seg = reinterpret_cast<T*>(p + L.seg);
+    s.stage = reinterpret_cast<EntRec<T>*>(p + L.stage);
+    s.clen = reinterpret_cast<int*>(p + L.clen);
+    s.cand_start = reinterpret_cast<int*>(p + L.cand_start);
+    s.chunk_first = reinterpret_cast<int*>(p + L.chunk_first);
+    s.row_n = reinterpret_cast<uint8_t*>(p + L.row_n);
+}
+
+template <typename T>
+__device__ inline EntRec<T> ld_rec(const EntRec<T>* p);
+template <>
+__device__ inline EntRec<float> ld_rec<float>(const EntRec<float>* p)
+{
+    float4 v = *reinterpret_cast<const float4*>(p);
+    EntRec<float> r;
+    r.meta = __float_as_uint(v.x);
+    r.f0 = v.y;
+    r.f1 = v.z;
+    r.f2 = v.w;
+    return r;
+}
+template <>
+__device__ inline EntRec<double> ld_rec<double>(const EntRec<double>* p)
+{
+    double2 u = reinterpret_cast<const double2*>(p)[0], v = reinterpret_cast<const double2*>(p)[1];
+    EntRec<double> r;
+    r.meta = (uint32_t)__double_as_longlong(u.x);
+    r.f0 = u.y;
+    r.f1 = v.x;
+    r.f2 = v.y;
+    return r;
+}
+template <typename T>
+__device__ inline void st_rec(EntRec<T>* p, uint32_t meta, T f0, T f1, T f2)
+{
+    p->meta = meta;
+    p->f0 = f0;
+    p->f1 = f1;
+    p->f2 = f2;
 }
 
 __device__ inline double warp_sum(double v)
@@ -216,25 +309,39 @@ __device__ inline int block_excl_scan(int v, int* red_i, int& total)
 // region).  Candidates: atom images of the node's tile whose box meets the
 // region, kept in tile-list order.  Entries: one per (candidate, region row
 // (y,z)) whose clipped support interval in x is non-empty, with the row's
-// y/z Gaussian factors.  Both entry orders are fixed (rows ascending within a
-// candidate; candidates ascending within a row), so every sum below has a
-// fixed order and results are bitwise reproducible.
+// y/z Gaussian factors.  Both entry orders are fixed (rows ascending within
+// a candidate; candidates ascending within a row), so every sum below has a
+// fixed order and results are bitwise reproducible.  Returns the candidate
+// count.
 // ------------------------------------------------------------------------
+
+// Clipped x-interval [xlo, xhi] (region columns) of box row (jj, kk) of a
+// candidate whose box starts at region column bx; false if empty.
 template <typename T, int M>
-__device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi, int qj, int qk,
-                        int* red_i)
+__device__ inline bool nl_row_interval(const NLParams<T>& nl, int atom, int bx, int jj, int kk, int& xlo, int& xhi)
+{
+    const uchar2 iv = *reinterpret_cast<const uchar2*>(nl.ivl + (((size_t)atom * nl.lb + jj) * nl.lb + kk) * 2);
+    xlo = max((int)iv.x + bx, 0);
+    xhi = min((int)iv.y + bx, Geo<M>::S - 1);
+    return iv.x <= iv.y && xlo <= xhi;
+}
+
+template <typename T, int M>
+__device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi, int qj, int qk, int* red_i)
 {
     using G = Geo<M>;
     const NLParams<T>& nl = a.nl;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int lb = nl.lb;
+    const int lim = nl.smem ? nl.ccap : MAX_CAND;
+    const int cap = G::S * G::S * ENTRIES_PER_ROW;
     int tile = (qi / TILE) + nl.ntile[0] * ((qj / TILE) + nl.ntile[1] * (qk / TILE));
     int beg = nl.tile_start[tile], end = nl.tile_start[tile + 1];
     // (1) candidates, ordered compaction of the tile list
     int ncand = 0;
     for (int c0 = beg; c0 < end; c0 += G::NT) {
         int c = c0 + tid;
-        int keep = 0;
+        int keep = 0, ln = 0;
         int4 rec = make_int4(0, 0, 0, 0);
         if (c < end) {
             int4 tc = nl.tile_cand[c];
@@ -243,138 +350,120 @@ __device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi,
             keep = (bx < G::S && bx + at.len[0] > 0 && by < G::S && by + at.len[1] > 0 &&
                     bz < G::S && bz + at.len[2] > 0);
             rec = make_int4(tc.x, bx, by, bz);
+            ln = at.len[0] | (at.len[1] << 8) | (at.len[2] << 16);
         }
         int tot;
         int pos = block_excl_scan<G::NW>(keep, red_i, tot);
         if (keep) {
-            if (ncand + pos < MAX_CAND) sc.cand[ncand + pos] = rec;
-            else atomicOr(a.err, ERR_CAPACITY);
+            if (ncand + pos < lim) {
+                sc.cand[ncand + pos] = rec;
+                sc.clen[ncand + pos] = ln;
+            } else {
+                atomicOr(a.err, ERR_CAPACITY);
+            }
         }
         ncand += tot;
     }
-    if (ncand > MAX_CAND) ncand = MAX_CAND;
-    const int nrow = G::S * G::S;
-    const int cap = nrow * ENTRIES_PER_ROW;
-    for (int r = tid; r < nrow; r += G::NT) sc.row_fill[r] = 0;
+    if (ncand > lim) ncand = lim;
+    for (int c = tid; c <= ncand; c += G::NT) sc.cand_start[c] = 0;     // entry counts first
     __syncthreads();
     // (2) x-tables of the candidates in region columns
     for (int i = tid; i < ncand * G::S; i += G::NT) {
         int c = i / G::S, x = i % G::S;
-        int4 rec = sc.cand[c];
-        int ii = x - rec.y;
+        int4 cr = sc.cand[c];
+        int ii = x - cr.y;
         T g = 0, dg = 0;
-        if (ii >= 0 && ii < nl.atoms[rec.x].len[0]) {
-            g = nl.G[(size_t)rec.x * 3 * lb + ii];
-            dg = nl.DG[(size_t)rec.x * 3 * lb + ii];
+        if (ii >= 0 && ii < (sc.clen[c] & 255)) {
+            g = nl.G[(size_t)cr.x * 3 * lb + ii];
+            dg = nl.DG[(size_t)cr.x * 3 * lb + ii];
         }
         sc.TX[2 * i] = g;
         sc.TX[2 * i + 1] = dg;
     }
-    // (3) entries: count per row and per candidate, scan, then fill (warp per
-    // candidate; rows of its box clipped to the region, ascending r)
-    for (int pass = 0; pass < 2; ++pass) {
-        for (int c = warp; c < ncand; c += G::NW) {
-            int4 rec = sc.cand[c];
-            AtomTab at = nl.atoms[rec.x];
-            const T* Gt = nl.G + (size_t)rec.x * 3 * lb;
-            const T* Dt = nl.DG + (size_t)rec.x * 3 * lb;
-            int j0 = max(0, -rec.z), j1 = min(at.len[1], G::S - rec.z);
-            int k0 = max(0, -rec.w), k1 = min(at.len[2], G::S - rec.w);
-            int nj = j1 - j0;
-            int nrows = (nj > 0 && k1 > k0) ? nj * (k1 - k0) : 0;
-            int cbase = pass ? sc.cand_start[c] : 0;
-            int cnt = 0;
-            for (int r0 = 0; r0 < nrows; r0 += 32) {
-                int rr = r0 + lane;
-                int ok = 0, xlo = 0, xhi = 0, row = 0, jj = 0, kk = 0;
-                if (rr < nrows) {
-                    jj = j0 + rr % nj;
-                    kk = k0 + rr / nj;
-                    const uint8_t* iv = nl.ivl + (((size_t)rec.x * lb + jj) * lb + kk) * 2;
-                    xlo = max((int)iv[0] + rec.y, 0);
-                    xhi = min((int)iv[1] + rec.y, G::S - 1);
-                    ok = (iv[0] <= iv[1]) && (xlo <= xhi);
-                    row = (rec.z + jj) + G::S * (rec.w + kk);
-                }
-                unsigned bal = __ballot_sync(0xffffffffu, ok);
-                if (ok) {
-                    if (!pass) {
-                        atomicAdd(&sc.row_fill[row], 1);
-                    } else {
-                        T gy = Gt[lb + jj], dgy = Dt[lb + jj], gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
-                        int ce = cbase + cnt + __popc(bal & ((1u << lane) - 1u));
-                        if (ce < cap) {
-                            sc.cent_meta[ce] = (uint32_t)row | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15);
-                            sc.cent_f[4 * ce + 0] = gy * gz;
-                            sc.cent_f[4 * ce + 1] = dgy * gz;
-                            sc.cent_f[4 * ce + 2] = gy * dgz;
-                            sc.cent_f[4 * ce + 3] = 0;
-                        }
-                        int se = sc.row_start[row] + atomicAdd(&sc.row_fill[row], 1);
-                        if (se < cap) {
-                            sc.ent_meta[se] = (uint32_t)c | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15);
-                            sc.ent_f[4 * se + 0] = gy * gz;
-                            sc.ent_f[4 * se + 1] = dgy * gz;
-                            sc.ent_f[4 * se + 2] = gy * dgz;
-                            sc.ent_f[4 * se + 3] = 0;
-                        }
-                    }
-                }
-                cnt += __popc(bal);
+    // (3) row-ordered entries: thread (lane = y, warp = z) tests the
+    // candidates in order for row (y, z); also counts every candidate's entries
+    if (lane < G::S) {
+        const int y = lane, z = warp;
+        const int r = y + G::S * z;
+        EntRec<T>* out = sc.rec + (size_t)r * ENTRIES_PER_ROW;
+        int n = 0;
+        for (int c = 0; c < ncand; ++c) {
+            const int4 cr = sc.cand[c];
+            const int ln = sc.clen[c];
+            const int jj = y - cr.z, kk = z - cr.w;
+            if (jj < 0 || jj >= ((ln >> 8) & 255) || kk < 0 || kk >= (ln >> 16)) continue;
+            int xlo, xhi;
+            if (!nl_row_interval<T, M>(nl, cr.x, cr.y, jj, kk, xlo, xhi)) continue;
+            if (n < ENTRIES_PER_ROW) {
+                const T* Gt = nl.G + (size_t)cr.x * 3 * lb;
+                const T* Dt = nl.DG + (size_t)cr.x * 3 * lb;
+                const T gy = Gt[lb + jj], dgy = Dt[lb + jj], gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
+                st_rec<T>(out + n, (uint32_t)c | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15), gy * gz, dgy * gz,
+                          gy * dgz);
+            } else {
+                atomicOr(a.err, ERR_CAPACITY);
             }
-            if (!pass && lane == 0) sc.cand_start[c] = cnt;
+            ++n;
+            atomicAdd(&sc.cand_start[c], 1);
         }
-        __syncthreads();
-        if (!pass) {
-            // exclusive scans: rows (counts in row_fill) and candidates
-            int run = 0;
-            for (int r0 = 0; r0 < nrow; r0 += G::NT) {
-                int r = r0 + tid;
-                int v = (r < nrow) ? sc.row_fill[r] : 0;
-                int tot;
-                int off = block_excl_scan<G::NW>(v, red_i, tot);
-                if (r < nrow) sc.row_start[r] = min(run + off, cap);
-                run += tot;
+        sc.row_n[r] = (uint8_t)min(n, ENTRIES_PER_ROW);
+    }
+    __syncthreads();
+    // (4) candidate offsets and chunk offsets (exclusive scans of the counts)
+    {
+        int run = 0, runk = 0;
+        for (int c0 = 0; c0 < ncand; c0 += G::NT) {
+            const int c = c0 + tid;
+            const int v = (c < ncand) ? sc.cand_start[c] : 0;
+            int tot, totk;
+            const int off = block_excl_scan<G::NW>(v, red_i, tot);
+            const int offk = block_excl_scan<G::NW>((v + 31) >> 5, red_i, totk);
+            if (c < ncand) {
+                sc.cand_start[c] = min(run + off, cap);
+                sc.chunk_first[c] = runk + offk;
             }
-            if (tid == 0) {
-                sc.row_start[nrow] = min(run, cap);
-                if (run > cap) atomicOr(a.err, ERR_CAPACITY);
-            }
-            run = 0;
-            for (int c0 = 0; c0 < ncand; c0 += G::NT) {
-                int c = c0 + tid;
-                int v = (c < ncand) ? sc.cand_start[c] : 0;
-                int tot;
-                int off = block_excl_scan<G::NW>(v, red_i, tot);
-                if (c < ncand) sc.cand_start[c] = min(run + off, cap);
-                run += tot;
-            }
-            if (tid == 0) sc.cand_start[ncand] = min(run, cap);
-            __syncthreads();
-            for (int r = tid; r < nrow; r += G::NT) sc.row_fill[r] = 0;
-            __syncthreads();
+            run += tot;
+            runk += totk;
+        }
+        if (tid == 0) {
+            if (run > cap) atomicOr(a.err, ERR_CAPACITY);
+            sc.cand_start[ncand] = min(run, cap);
+            sc.chunk_first[ncand] = runk;
         }
     }
-    // (4) order each row's entries by candidate (a handful per row)
-    for (int r = tid; r < nrow; r += G::NT) {
-        int b = sc.row_start[r], n = sc.row_start[r + 1] - b;
-        uint32_t* Mt = sc.ent_meta + b;
-        T* F = sc.ent_f + 4 * (size_t)b;
-        for (int i = 1; i < n; ++i) {
-            uint32_t v = Mt[i];
-            T f0 = F[4 * i], f1 = F[4 * i + 1], f2 = F[4 * i + 2];
-            int j = i - 1;
-            while (j >= 0 && (Mt[j] & 1023u) > (v & 1023u)) {
-                Mt[j + 1] = Mt[j];
-                F[4 * (j + 1)] = F[4 * j];
-                F[4 * (j + 1) + 1] = F[4 * j + 1];
-                F[4 * (j + 1) + 2] = F[4 * j + 2];
-                --j;
+    __syncthreads();
+    // (5) candidate-ordered entries: warp per candidate, its box rows clipped
+    // to the region in ascending r, compacted with a ballot
+    for (int c = warp; c < ncand; c += G::NW) {
+        const int4 cr = sc.cand[c];
+        const int ln = sc.clen[c];
+        const T* Gt = nl.G + (size_t)cr.x * 3 * lb;
+        const T* Dt = nl.DG + (size_t)cr.x * 3 * lb;
+        const int j0 = max(0, -cr.z), j1 = min((ln >> 8) & 255, G::S - cr.z);
+        const int k0 = max(0, -cr.w), k1 = min(ln >> 16, G::S - cr.w);
+        const int nj = j1 - j0;
+        const int nrows = (nj > 0 && k1 > k0) ? nj * (k1 - k0) : 0;
+        const int cbase = sc.cand_start[c], cend = sc.cand_start[c + 1];
+        int cnt = 0;
+        for (int r0 = 0; r0 < nrows; r0 += 32) {
+            const int rr = r0 + lane;
+            int ok = 0, xlo = 0, xhi = 0, jj = 0, kk = 0;
+            if (rr < nrows) {
+                jj = j0 + rr % nj;
+                kk = k0 + rr / nj;
+                ok = nl_row_interval<T, M>(nl, cr.x, cr.y, jj, kk, xlo, xhi);
             }
-            Mt[j + 1] = v;
-            F[4 * (j + 1)] = f0;
-            F[4 * (j + 1) + 1] = f1;
-            F[4 * (j + 1) + 2] = f2;
+            const unsigned bal = __ballot_sync(0xffffffffu, ok);
+            if (ok) {
+                const int ce = cbase + cnt + __popc(bal & ((1u << lane) - 1u));
+                if (ce < cend) {
+                    const int row = (cr.z + jj) + G::S * (cr.w + kk);
+                    const T gy = Gt[lb + jj], dgy = Dt[lb + jj], gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
+                    st_rec<T>(sc.cent + ce, (uint32_t)row | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15), gy * gz,
+                              dgy * gz, gy * dgz);
+                }
+            }
+            cnt += __popc(bal);
         }
     }
     __syncthreads();
@@ -385,85 +474,208 @@ __device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi,
 // Eq. IntApprox, without the h^3 which sits in cs/cp):
 //   S_c = sum G t, X_c = sum D_x G t, Y_c = sum D_y G t, Z_c = sum D_z G t
 // over the support of candidate c inside the region.  The Gaussian factorises
-// per axis: each row is reduced along x with the x-table, then weighted by the
-// row's y/z factors.  One warp per candidate, lanes over its rows, a
-// warp-uniform x loop (table values are broadcasts), warp tree at the end.
+// per axis: each row is reduced along x with the candidate's x-profile, then
+// weighted by the row's y/z factors.  The candidate-ordered entries are cut
+// into chunks of 32 (one entry per lane) and each warp takes a contiguous run
+// of chunks, so the warps carry equal work whatever the candidates' sizes;
+// the next chunk's records are fetched while the current one is reduced.  A
+// warp's partial sums for candidate c go to seg[c + warp] -- distinct for
+// every (candidate, warp) pair that occurs, because both rise along the chunk
+// order -- and nl_collect adds them in warp order, so the order is fixed.
+constexpr int LBMAX = 20;    // unrolled box width (longer boxes take the plain loop)
+
+template <typename T>
+struct Pair2;
+template <> struct Pair2<float> { using type = float2; };
+template <> struct Pair2<double> { using type = double2; };
+
 template <typename T, int M>
 __device__ void nl_dots(const RegionArgs<T>& a, const CtaScratch<T>& sc, const T* cur, int ncand)
 {
     using G = Geo<M>;
+    using P2 = typename Pair2<T>::type;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = warp; c < ncand; c += G::NW) {
-        int4 rec = sc.cand[c];
-        const int x0 = max(rec.y, 0), x1 = min(rec.y + a.nl.atoms[rec.x].len[0], G::S) - 1;
-        const T* tx = sc.TX + (size_t)c * G::S * 2;
-        const int e0 = sc.cand_start[c], e1 = sc.cand_start[c + 1];
-        T aS = 0, aX = 0, aY = 0, aZ = 0;
-        for (int eb = e0; eb < e1; eb += 32) {
-            const int e = eb + lane;
-            const bool valid = e < e1;
-            uint32_t mt = valid ? sc.cent_meta[e] : 0u;
-            int r = mt & 1023u, xlo = valid ? (int)((mt >> 10) & 31u) : 1, xhi = (mt >> 15) & 31u;
-            int y = r % G::S, z = r / G::S;
-            const T* row = cur + G::LEAD + z * G::PLANE + y * G::PX;
-            T u = 0, u2 = 0;
-            for (int x = x0; x <= x1; ++x) {
-                T g = tx[2 * x], dg = tx[2 * x + 1];
-                T tv = (x >= xlo && x <= xhi) ? row[x] : T(0);
-                u += g * tv;
-                u2 += dg * tv;
-            }
-            if (valid) {
-                T f0 = sc.cent_f[4 * e], f1 = sc.cent_f[4 * e + 1], f2 = sc.cent_f[4 * e + 2];
-                aS += f0 * u;
-                aX += f0 * u2;
-                aY += f1 * u;
-                aZ += f2 * u;
-            }
+    const int K = sc.chunk_first[ncand];
+    const int Q = (K + G::NW - 1) / G::NW;
+    const int j0 = warp * Q, j1 = min(K, j0 + Q);
+    if (j0 >= j1) return;
+    int lo = 0, hi = ncand - 1;                       // last candidate with chunk_first <= j0
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sc.chunk_first[mid] <= j0) lo = mid;
+        else hi = mid - 1;
+    }
+    const bool unrolled = a.nl.lb <= LBMAX;
+    // records of chunks j+1 and j+2 are in flight while chunk j is reduced
+    auto fetch = [&](int j, int c, EntRec<T>& r, bool& v) {
+        const int e = sc.cand_start[c] + (j - sc.chunk_first[c]) * 32 + lane;
+        v = e < sc.cand_start[c + 1];
+        if (v) r = ld_rec(sc.cent + e);
+    };
+    EntRec<T> rA, rB;
+    rA.meta = rB.meta = 0;
+    rA.f0 = rA.f1 = rA.f2 = rB.f0 = rB.f1 = rB.f2 = 0;
+    bool vA = false, vB = false;
+    int cA = lo, cB = lo;
+    fetch(j0, cA, rA, vA);
+    if (j0 + 1 < j1) {
+        while (j0 + 1 >= sc.chunk_first[cB + 1]) ++cB;
+        fetch(j0 + 1, cB, rB, vB);
+    }
+    T aS = 0, aX = 0, aY = 0, aZ = 0;
+    for (int j = j0; j < j1; ++j) {
+        const EntRec<T> rc = rA;
+        const bool val = vA;
+        const int c = cA;
+        rA = rB;
+        vA = vB;
+        cA = cB;
+        if (j + 2 < j1) {
+            while (j + 2 >= sc.chunk_first[cB + 1]) ++cB;
+            fetch(j + 2, cB, rB, vB);
         }
-        aS = warp_sumT<T>(aS);
-        aX = warp_sumT<T>(aX);
-        aY = warp_sumT<T>(aY);
-        aZ = warp_sumT<T>(aZ);
-        if (lane == 0) {
-            sc.P[4 * c + 0] = aS;
-            sc.P[4 * c + 1] = aX;
-            sc.P[4 * c + 2] = aY;
-            sc.P[4 * c + 3] = aZ;
+        if (val) {
+            const int r = rc.meta & 1023u, xlo = (rc.meta >> 10) & 31u, xhi = (rc.meta >> 15) & 31u;
+            const int y = r % G::S, z = r / G::S;
+            const T* row = cur + G::LEAD + z * G::PLANE + y * G::PX;
+            const P2* tx = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * G::S;
+            T u = 0, u2 = 0;
+            if (unrolled) {
+                // slots k of the candidate's box, x = bx + k: every lane of the
+                // chunk reads the same (G, DG) pair, and rows of one plane sit
+                // in distinct banks
+                const int bx = sc.cand[c].y;
+                const T* rowp = row + bx;
+                const P2* txp = tx + bx;
+                const uint32_t mask = ((2u << (xhi - bx)) - 1u) & ~((1u << (xlo - bx)) - 1u);
+#pragma unroll
+                for (int k = 0; k < LBMAX; ++k)
+                    if (mask & (1u << k)) {
+                        const P2 g = txp[k];
+                        const T tv = rowp[k];
+                        u += g.x * tv;
+                        u2 += g.y * tv;
+                    }
+            } else {
+                for (int x = xlo; x <= xhi; ++x) {
+                    const P2 g = tx[x];
+                    const T tv = row[x];
+                    u += g.x * tv;
+                    u2 += g.y * tv;
+                }
+            }
+            aS += rc.f0 * u;
+            aX += rc.f0 * u2;
+            aY += rc.f1 * u;
+            aZ += rc.f2 * u;
+        }
+        if (j + 1 >= j1 || cA != c) {                 // warp-uniform: candidate done in this warp
+            aS = warp_sumT<T>(aS);                    // xor tree: every lane holds the totals
+            aX = warp_sumT<T>(aX);
+            aY = warp_sumT<T>(aY);
+            aZ = warp_sumT<T>(aZ);
+            if (lane == 0) {
+                T* sg = sc.seg + (size_t)(c + warp) * 4;
+                sg[0] = aS;
+                sg[1] = aX;
+                sg[2] = aY;
+                sg[3] = aZ;
+            }
+            aS = aX = aY = aZ = 0;
         }
     }
 }
 
-// V_nl t at region column x of row r (warp-uniform loop over the row's
-// entries; candidates in fixed order):
-//   sum_c h^3 G_x [ f0 (gamma_s A_s^2 S_c + ...) ] =
-//   sum_e TX_c(x) . (b0, b1),  b0 = cs f0 S + cp (f1 Y + f2 Z),  b1 = cp f0 X
+// P_c = sum over the warps that reduced part of candidate c of their partial
+// sums, in warp order.
 template <typename T, int M>
-__device__ inline T nl_row_apply(const RegionArgs<T>& a, const CtaScratch<T>& sc, int r, int x)
+__device__ void nl_collect(const CtaScratch<T>& sc, int ncand)
 {
     using G = Geo<M>;
-    const int e0 = sc.row_start[r], e1 = sc.row_start[r + 1];
-    const T cs = a.nl.cs, cp = a.nl.cp;
-    T acc = 0;
-    for (int e = e0; e < e1; ++e) {
-        uint32_t mt = sc.ent_meta[e];
-        int c = mt & 1023u, xlo = (mt >> 10) & 31u, xhi = (mt >> 15) & 31u;
-        T f0 = sc.ent_f[4 * e], f1 = sc.ent_f[4 * e + 1], f2 = sc.ent_f[4 * e + 2];
-        T pS = sc.P[4 * c], pX = sc.P[4 * c + 1], pY = sc.P[4 * c + 2], pZ = sc.P[4 * c + 3];
-        T b0 = cs * f0 * pS + cp * (f1 * pY + f2 * pZ);
-        T b1 = cp * f0 * pX;
-        const T* tx = sc.TX + ((size_t)c * G::S + x) * 2;
-        T g = (x >= xlo && x <= xhi) ? tx[0] : T(0);
-        T dg = (x >= xlo && x <= xhi) ? tx[1] : T(0);
-        acc += g * b0 + dg * b1;
+    const int K = sc.chunk_first[ncand];
+    const int Q = (K + G::NW - 1) / G::NW;
+    for (int c = threadIdx.x; c < ncand; c += G::NT) {
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        const int f0 = sc.chunk_first[c], f1 = sc.chunk_first[c + 1];
+        if (f1 > f0)
+            for (int w = f0 / Q; w <= (f1 - 1) / Q; ++w) {
+                const T* sg = sc.seg + (size_t)(c + w) * 4;
+                s0 += sg[0];
+                s1 += sg[1];
+                s2 += sg[2];
+                s3 += sg[3];
+            }
+        sc.P[4 * c + 0] = s0;
+        sc.P[4 * c + 1] = s1;
+        sc.P[4 * c + 2] = s2;
+        sc.P[4 * c + 3] = s3;
     }
-    return acc;
+}
+
+// sec <- a_old * sec - coef * V_nl t.  Warp z takes the rows (y, z) of
+// plane z in turn, lane = x.  For a row, lane j computes the coefficients of
+// entry j,
+//   b0 = coef (cs f0 S_c + cp (f1 Y_c + f2 Z_c)),  b1 = coef cp f0 X_c,
+// and stages them in shared memory; then every lane adds, over the row's
+// entries (candidates ascending, a fixed order), G_x b0 + DG_x b1 where its
+// x lies in the entry's interval, and updates its point once.  Reads are
+// broadcasts (the staged entry) or contiguous (the x-table row of the entry's
+// candidate); the next row's records are fetched while this one is summed.
+template <typename T, int M, bool DB>
+__device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* sec, T a_old, T coef)
+{
+    using G = Geo<M>;
+    using P2 = typename Pair2<T>::type;
+    const int lane = threadIdx.x & 31, z = threadIdx.x >> 5;
+    const bool own = lane < G::S;
+    const T cs = a.nl.cs * coef, cp = a.nl.cp * coef;
+    const P2* tx2 = reinterpret_cast<const P2*>(sc.TX);
+    EntRec<T>* stg = sc.stage + z * STAGE;
+    const EntRec<T>* recz = sc.rec + (size_t)(G::S * z) * ENTRIES_PER_ROW;
+    EntRec<T> nxt;
+    nxt.meta = 0;
+    nxt.f0 = nxt.f1 = nxt.f2 = 0;
+    if (lane < STAGE) nxt = ld_rec(recz + lane);     // (slots past the row's count are ignored)
+    for (int y = 0; y < G::S; ++y) {
+        const int n = sc.row_n[y + G::S * z];
+        const EntRec<T> first = nxt;
+        if (y + 1 < G::S && lane < STAGE) nxt = ld_rec(recz + (size_t)(y + 1) * ENTRIES_PER_ROW + lane);
+        T acc = 0;
+        for (int eb = 0; eb < n; eb += STAGE) {
+            EntRec<T> rc = first;
+            if (eb > 0 && lane < STAGE && eb + lane < ENTRIES_PER_ROW)
+                rc = ld_rec(recz + (size_t)y * ENTRIES_PER_ROW + eb + lane);
+            const int cnt = min(STAGE, n - eb);
+            if (lane < cnt) {
+                const T* Pc = sc.P + 4 * (rc.meta & 1023u);
+                const T b0 = cs * rc.f0 * Pc[0] + cp * (rc.f1 * Pc[2] + rc.f2 * Pc[3]);
+                const T b1 = cp * rc.f0 * Pc[1];
+                st_rec<T>(stg + lane, rc.meta, b0, b1, T(0));
+            }
+            __syncwarp();
+            for (int k = 0; k < cnt; ++k) {
+                const EntRec<T> e = ld_rec(stg + k);
+                const int c = e.meta & 1023u, xlo = (e.meta >> 10) & 31u, xhi = (e.meta >> 15) & 31u;
+                if (lane >= xlo && lane <= xhi) {
+                    const P2 g = tx2[(size_t)c * G::S + lane];
+                    acc += g.x * e.f0 + g.y * e.f1;
+                }
+            }
+            __syncwarp();
+        }
+        if (own) {
+            T* bp = Sec<M, DB>::row(sec, y, z) + lane;
+            const T old = (a_old == T(0)) ? T(0) : (a_old == T(1) ? *bp : a_old * *bp);
+            *bp = old - acc;
+        }
+    }
 }
 
 // ------------------------------------------------------------------------
-// Stencil sweep of H (Eq. FD:Laplacian + V, plus the projector term):
-//   out(p) = s * [ (-3 w_0 + V(p) - shift) t(p) - 1/2 sum_d w_d (6 nbrs at d)
-//                  + (V_nl t)(p) ] - a_old * sec(p)
+// Stencil sweep of H (local part, Eq. FD:Laplacian + V):
+//   out(p) = s * [ (-3 w_0 + V(p) - shift) t(p) - 1/2 sum_d w_d (6 nbrs at d) ] - a_old * sec(p)
+// (the projector term, when present, has already been folded into sec by
+// nl_update, and a_old is then 1)
 // RECUR = true (Chebyshev step): out = t^{i+1} and sec holds t^{i-1}.
 //   DB:  out replaces t^{i-1} in sec (pointwise, no barrier); the caller
 //        swaps the two buffers after the sweep.
@@ -475,8 +687,8 @@ __device__ inline T nl_row_apply(const RegionArgs<T>& a, const CtaScratch<T>& sc
 //   thread accumulates out.t.
 // ------------------------------------------------------------------------
 template <typename T, int M, bool RECUR, bool DB>
-__device__ void stencil_sweep(const RegionArgs<T>& a, const CtaScratch<T>& sc, bool has_nl, T* cur, T* sec,
-                              const T* vwin, T s, T a_old, T dshift, T& acc_a, T& acc_b, double* centre_out)
+__device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* vwin, T s, T a_old, T dshift,
+                              T& acc_a, T& acc_b, double* centre_out)
 {
     using G = Geo<M>;
     using SV = Sec<M, DB>;
@@ -506,7 +718,6 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, const CtaScratch<T>& sc, b
             }
             T vz = vcol[z * vplane];
             T hv = (vz + dshift) * c + lap;
-            if (has_nl) hv += nl_row_apply<T, M>(a, sc, y + G::S * z, x);
             out = s * hv - a_old * bcol[z * SV::ZS];
         }
         if (RECUR && !DB) __syncthreads();
@@ -542,12 +753,14 @@ moments_kernel(RegionArgs<T> a)
     T* bufA = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[2][2][32];          // [step parity][d2, d1][warp]
     __shared__ int red_i[33];
-    __shared__ double s_mom[MAX_NPL / 2 + 2];
-    __shared__ double s_d2[MAX_NPL / 2 + 2];
-    __shared__ double s_d1[MAX_NPL / 2 + 2];
+    // after the region vectors: rho^i and the two product sums (npl/2 + 2 each), then the projector tables
+    double* s_mom = reinterpret_cast<double*>(smem_raw + align16(region_smem<T, M>()));
+    double* s_d2 = s_mom + (a.npl / 2 + 2);
+    double* s_d1 = s_d2 + (a.npl / 2 + 2);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const CtaScratch<T> sc = cta_scratch(a, M);
+    CtaScratch<T> sc = cta_scratch(a, M);
+    if (a.nl.smem) nl_tables_in_smem(sc, s_d1 + (a.npl / 2 + 2), a.nl.ccap, G::S);
     T* bufB = DB ? bufA + G::ELEMS : sc.buf;
     const int half = a.npl / 2;
     const bool has_nl = a.nl.n_atoms > 0;
@@ -578,13 +791,18 @@ moments_kernel(RegionArgs<T> a)
         T* sec = bufB;
         for (int i = 0; i < half; ++i) {
             const T s = (i == 0) ? s1 : s2;
+            const T a_old = (i == 0) ? T(0) : T(1);
             if (has_nl) {
                 nl_dots<T, M>(a, sc, cur, ncand);
                 __syncthreads();
+                nl_collect<T, M>(sc, ncand);
+                __syncthreads();
+                nl_update<T, M, DB>(a, sc, sec, a_old, s);
+                __syncthreads();
             }
             T aa, ab;
-            stencil_sweep<T, M, true, DB>(a, sc, has_nl, cur, sec, vwin, s, (i == 0) ? T(0) : T(1), dshift, aa,
-                                          ab, &s_mom[i + 1]);
+            stencil_sweep<T, M, true, DB>(a, cur, sec, vwin, s, has_nl ? T(1) : a_old, dshift, aa, ab,
+                                          &s_mom[i + 1]);
             // t^{i+1}.t^{i+1} and t^{i+1}.t^i: column sums in T, warp trees, FP64 across warps
             const int par = i & 1;
             double w2 = warp_total(aa), w1 = warp_total(ab);
@@ -637,7 +855,8 @@ lanczos_kernel(RegionArgs<T> a)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int x = lane, y = warp;
     const bool active = x < G::S;
-    const CtaScratch<T> sc = cta_scratch(a, M);
+    CtaScratch<T> sc = cta_scratch(a, M);
+    if (a.nl.smem) nl_tables_in_smem(sc, smem_raw + region_smem<T, M>(), a.nl.ccap, G::S);
     T* sec = DB ? sm + G::ELEMS : sc.buf;
     const bool has_nl = a.nl.n_atoms > 0;
     const T dshift = (T)(-3.0 * a.g.w[0]);
@@ -669,9 +888,14 @@ lanczos_kernel(RegionArgs<T> a)
             if (has_nl) {
                 nl_dots<T, M>(a, sc, sm, ncand);
                 __syncthreads();
+                nl_collect<T, M>(sc, ncand);
+                __syncthreads();
+                nl_update<T, M, DB>(a, sc, sec, bprevT, T(1));
+                __syncthreads();
             }
             T aa, ab;
-            stencil_sweep<T, M, false, DB>(a, sc, has_nl, sm, sec, vwin, T(1), bprevT, dshift, aa, ab, &s_dummy);
+            stencil_sweep<T, M, false, DB>(a, sm, sec, vwin, T(1), has_nl ? T(1) : bprevT, dshift, aa, ab,
+                                           &s_dummy);
             double wt = warp_total(ab);
             if (lane == 0) red_a[warp] = wt;
             __syncthreads();
@@ -725,10 +949,5 @@ lanczos_kernel(RegionArgs<T> a)
     }
 }
 
-template <typename T, int M>
-size_t region_smem()
-{
-    return (fits_double_buffer<T, M>() ? 2 : 1) * (size_t)Geo<M>::ELEMS * sizeof(T);
-}
 
 }  // namespace sq

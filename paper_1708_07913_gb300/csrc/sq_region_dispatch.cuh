@@ -10,13 +10,15 @@ namespace sq {
 template <typename T>
 struct RegionDispatch {
     template <int M>
-    static int config(int which, int* blocks_per_sm, size_t* smem)
+    static int config(int which, size_t extra, int* blocks_per_sm, size_t* smem)
     {
         constexpr bool DB = fits_double_buffer<T, M>();
-        size_t bytes = region_smem<T, M>();
+        size_t bytes = region_smem<T, M>() + extra;
         const void* fn = which == 0 ? (const void*)moments_kernel<T, M, DB> : (const void*)lanczos_kernel<T, M, DB>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess)
-            return SQ_ECUDA;
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return SQ_EUNSUPPORTED;
+        }
         int occ = 0;
         if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, Geo<M>::NT, bytes) != cudaSuccess)
             return SQ_ECUDA;
@@ -25,10 +27,10 @@ struct RegionDispatch {
         return occ > 0 ? SQ_OK : SQ_EUNSUPPORTED;
     }
     template <int M>
-    static int launch(int which, const RegionArgs<T>& a, int blocks, cudaStream_t st)
+    static int launch(int which, const RegionArgs<T>& a, size_t extra, int blocks, cudaStream_t st)
     {
         constexpr bool DB = fits_double_buffer<T, M>();
-        size_t bytes = region_smem<T, M>();
+        size_t bytes = region_smem<T, M>() + extra;
         if (which == 0) moments_kernel<T, M, DB><<<blocks, Geo<M>::NT, bytes, st>>>(a);
         else lanczos_kernel<T, M, DB><<<blocks, Geo<M>::NT, bytes, st>>>(a);
         return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;

@@ -4,20 +4,20 @@
 namespace sq {
 using D32 = RegionDispatch<float>;
 
-int region_config_f32(int m, int which, int* bps, size_t* smem)
+int region_config_f32(int m, int which, size_t extra, int* bps, size_t* smem)
 {
     switch (m) {
-#define C(M) case M: return D32::config<M>(which, bps, smem);
+#define C(M) case M: return D32::config<M>(which, extra, bps, smem);
         C(0) C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13) C(14) C(15)
 #undef C
     }
     return SQ_EUNSUPPORTED;
 }
 
-int region_launch_f32(int m, int which, const RegionArgs<float>& a, int blocks, cudaStream_t st)
+int region_launch_f32(int m, int which, const RegionArgs<float>& a, size_t extra, int blocks, cudaStream_t st)
 {
     switch (m) {
-#define C(M) case M: return D32::launch<M>(which, a, blocks, st);
+#define C(M) case M: return D32::launch<M>(which, a, extra, blocks, st);
         C(0) C(1) C(2) C(3) C(4) C(5) C(6) C(7) C(8) C(9) C(10) C(11) C(12) C(13) C(14) C(15)
 #undef C
     }
