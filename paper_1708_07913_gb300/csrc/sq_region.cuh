@@ -612,61 +612,100 @@ __device__ void nl_collect(const CtaScratch<T>& sc, int ncand)
     }
 }
 
-// sec <- a_old * sec - coef * V_nl t.  Warp z takes the rows (y, z) of
-// plane z in turn, lane = x.  For a row, lane j computes the coefficients of
-// entry j,
+// The four inner products of candidate c (one 16-byte load in FP32).
+template <typename T>
+__device__ inline void load_P(const T* P, int c, T& pS, T& pX, T& pY, T& pZ);
+template <>
+__device__ inline void load_P<float>(const float* P, int c, float& pS, float& pX, float& pY, float& pZ)
+{
+    const float4 v = reinterpret_cast<const float4*>(P)[c];
+    pS = v.x;
+    pX = v.y;
+    pY = v.z;
+    pZ = v.w;
+}
+template <>
+__device__ inline void load_P<double>(const double* P, int c, double& pS, double& pX, double& pY, double& pZ)
+{
+    const double2 u = reinterpret_cast<const double2*>(P)[2 * c], v = reinterpret_cast<const double2*>(P)[2 * c + 1];
+    pS = u.x;
+    pX = u.y;
+    pY = v.x;
+    pZ = v.y;
+}
+
+// sec <- a_old * sec - coef * V_nl t.  Thread (lane = y, warp = z) owns
+// region row (y, z) and walks its entries (candidates ascending); the lanes
+// of a warp take their k-th entries together, and each entry's x-interval is
+// covered by predicated slots, loads first and stores after, so every entry
+// costs a fixed, overlapped instruction sequence.  Per entry
 //   b0 = coef (cs f0 S_c + cp (f1 Y_c + f2 Z_c)),  b1 = coef cp f0 X_c,
-// and stages them in shared memory; then every lane adds, over the row's
-// entries (candidates ascending, a fixed order), G_x b0 + DG_x b1 where its
-// x lies in the entry's interval, and updates its point once.  Reads are
-// broadcasts (the staged entry) or contiguous (the x-table row of the entry's
-// candidate); the next row's records are fetched while this one is summed.
+// and each point of the interval gets  -= G_x b0 + DG_x b1.  The lanes own
+// neighbouring rows of one plane, whose candidates and intervals nearly
+// coincide, so their shared-memory accesses spread over distinct banks.
 template <typename T, int M, bool DB>
 __device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* sec, T a_old, T coef)
 {
     using G = Geo<M>;
     using P2 = typename Pair2<T>::type;
-    const int lane = threadIdx.x & 31, z = threadIdx.x >> 5;
+    constexpr int GRP = sizeof(T) == 4 ? 5 : 4;       // slots loaded together (divides LBMAX)
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool own = lane < G::S;
+    const int r = (own ? lane : 0) + G::S * warp;
+    T* brow = Sec<M, DB>::row(sec, own ? lane : 0, warp);
+    if (own && a_old != T(1))
+        for (int x = 0; x < G::S; ++x) brow[x] = (a_old == T(0)) ? T(0) : a_old * brow[x];
+    const int n = own ? sc.row_n[r] : 0;
+    const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
+    if (nmax == 0) return;
+    const bool unrolled = a.nl.lb <= LBMAX;
     const T cs = a.nl.cs * coef, cp = a.nl.cp * coef;
     const P2* tx2 = reinterpret_cast<const P2*>(sc.TX);
-    EntRec<T>* stg = sc.stage + z * STAGE;
-    const EntRec<T>* recz = sc.rec + (size_t)(G::S * z) * ENTRIES_PER_ROW;
-    EntRec<T> nxt;
-    nxt.meta = 0;
-    nxt.f0 = nxt.f1 = nxt.f2 = 0;
-    if (lane < STAGE) nxt = ld_rec(recz + lane);     // (slots past the row's count are ignored)
-    for (int y = 0; y < G::S; ++y) {
-        const int n = sc.row_n[y + G::S * z];
-        const EntRec<T> first = nxt;
-        if (y + 1 < G::S && lane < STAGE) nxt = ld_rec(recz + (size_t)(y + 1) * ENTRIES_PER_ROW + lane);
-        T acc = 0;
-        for (int eb = 0; eb < n; eb += STAGE) {
-            EntRec<T> rc = first;
-            if (eb > 0 && lane < STAGE && eb + lane < ENTRIES_PER_ROW)
-                rc = ld_rec(recz + (size_t)y * ENTRIES_PER_ROW + eb + lane);
-            const int cnt = min(STAGE, n - eb);
-            if (lane < cnt) {
-                const T* Pc = sc.P + 4 * (rc.meta & 1023u);
-                const T b0 = cs * rc.f0 * Pc[0] + cp * (rc.f1 * Pc[2] + rc.f2 * Pc[3]);
-                const T b1 = cp * rc.f0 * Pc[1];
-                st_rec<T>(stg + lane, rc.meta, b0, b1, T(0));
-            }
-            __syncwarp();
-            for (int k = 0; k < cnt; ++k) {
-                const EntRec<T> e = ld_rec(stg + k);
-                const int c = e.meta & 1023u, xlo = (e.meta >> 10) & 31u, xhi = (e.meta >> 15) & 31u;
-                if (lane >= xlo && lane <= xhi) {
-                    const P2 g = tx2[(size_t)c * G::S + lane];
-                    acc += g.x * e.f0 + g.y * e.f1;
+    const EntRec<T>* rrow = sc.rec + (size_t)r * ENTRIES_PER_ROW;
+    EntRec<T> r0, r1;
+    r0.meta = r1.meta = 0;
+    r0.f0 = r0.f1 = r0.f2 = r1.f0 = r1.f1 = r1.f2 = 0;
+    if (n > 0) r0 = ld_rec(rrow);
+    if (n > 1) r1 = ld_rec(rrow + 1);
+    for (int k = 0; k < nmax; ++k) {
+        const EntRec<T> rc = r0;
+        r0 = r1;
+        if (k + 2 < n) r1 = ld_rec(rrow + k + 2);
+        if (k >= n) continue;
+        const int c = rc.meta & 1023u, xlo = (rc.meta >> 10) & 31u, xhi = (rc.meta >> 15) & 31u;
+        T pS, pX, pY, pZ;
+        load_P<T>(sc.P, c, pS, pX, pY, pZ);
+        const T b0 = cs * rc.f0 * pS + cp * (rc.f1 * pY + rc.f2 * pZ);
+        const T b1 = cp * rc.f0 * pX;
+        const P2* tx = tx2 + (size_t)c * G::S + xlo;
+        T* bp = brow + xlo;
+        const int len = xhi - xlo;                    // slots 0..len
+        bool done = false;
+        if constexpr (sizeof(T) == 4) {               // FP64 takes the plain loop: registers matter more there
+            if (unrolled) {
+#pragma unroll
+                for (int h = 0; h < LBMAX / GRP; ++h) {
+                    if (h * GRP > len) break;
+                    P2 g[GRP];
+                    T v[GRP];
+#pragma unroll
+                    for (int s = 0; s < GRP; ++s)
+                        if (h * GRP + s <= len) {
+                            g[s] = tx[h * GRP + s];
+                            v[s] = bp[h * GRP + s];
+                        }
+#pragma unroll
+                    for (int s = 0; s < GRP; ++s)
+                        if (h * GRP + s <= len) bp[h * GRP + s] = v[s] - (g[s].x * b0 + g[s].y * b1);
                 }
+                done = true;
             }
-            __syncwarp();
         }
-        if (own) {
-            T* bp = Sec<M, DB>::row(sec, y, z) + lane;
-            const T old = (a_old == T(0)) ? T(0) : (a_old == T(1) ? *bp : a_old * *bp);
-            *bp = old - acc;
+        if (!done) {
+            for (int s = 0; s <= len; ++s) {
+                const P2 g = tx[s];
+                bp[s] -= g.x * b0 + g.y * b1;
+            }
         }
     }
 }
