@@ -634,7 +634,8 @@ __device__ inline void load_P<double>(const double* P, int c, double& pS, double
     pZ = v.y;
 }
 
-// sec <- a_old * sec - coef * V_nl t.  Thread (lane = y, warp = z) owns
+// sec <- sec - coef * V_nl t, candidate-ordered per point (FP64; the FP32
+// form uses nl_update_red below).  Thread (lane = y, warp = z) owns
 // region row (y, z) and walks its entries (candidates ascending); the lanes
 // of a warp take their k-th entries together, and each entry's x-interval is
 // covered by predicated slots, loads first and stores after, so every entry
@@ -644,7 +645,7 @@ __device__ inline void load_P<double>(const double* P, int c, double& pS, double
 // neighbouring rows of one plane, whose candidates and intervals nearly
 // coincide, so their shared-memory accesses spread over distinct banks.
 template <typename T, int M, bool DB>
-__device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* sec, T a_old, T coef)
+__device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* sec, T coef)
 {
     using G = Geo<M>;
     using P2 = typename Pair2<T>::type;
@@ -653,8 +654,6 @@ __device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* se
     const bool own = lane < G::S;
     const int r = (own ? lane : 0) + G::S * warp;
     T* brow = Sec<M, DB>::row(sec, own ? lane : 0, warp);
-    if (own && a_old != T(1))
-        for (int x = 0; x < G::S; ++x) brow[x] = (a_old == T(0)) ? T(0) : a_old * brow[x];
     const int n = own ? sc.row_n[r] : 0;
     const int nmax = __reduce_max_sync(0xffffffffu, (unsigned)n);
     if (nmax == 0) return;
@@ -710,11 +709,95 @@ __device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* se
     }
 }
 
+// sec <- sec - coef * V_nl t for the FP32 form: the update walks the
+// candidate-ordered entries exactly like nl_dots (equal runs of 32-entry
+// chunks per warp, one entry per lane, slots from the candidate's box start,
+// records two chunks ahead), and adds each point's contribution with a
+// shared-memory atomic add.  Lanes of a chunk own distinct rows; points
+// covered by several candidates receive their contributions in an order
+// that varies from run to run, so this form is reproducible to FP32
+// rounding rather than bitwise (the FP64 form keeps the fixed order).
+template <typename T, int M, bool DB>
+__device__ void nl_update_red(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* sec, int ncand, T coef)
+{
+    using G = Geo<M>;
+    using P2 = typename Pair2<T>::type;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int K = sc.chunk_first[ncand];
+    const int Q = (K + G::NW - 1) / G::NW;
+    const int j0 = warp * Q, j1 = min(K, j0 + Q);
+    if (j0 >= j1) return;
+    int lo = 0, hi = ncand - 1;                       // last candidate with chunk_first <= j0
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (sc.chunk_first[mid] <= j0) lo = mid;
+        else hi = mid - 1;
+    }
+    const bool unrolled = a.nl.lb <= LBMAX;
+    const T cs = a.nl.cs * coef, cp = a.nl.cp * coef;
+    auto fetch = [&](int j, int c, EntRec<T>& r, bool& v) {
+        const int e = sc.cand_start[c] + (j - sc.chunk_first[c]) * 32 + lane;
+        v = e < sc.cand_start[c + 1];
+        if (v) r = ld_rec(sc.cent + e);
+    };
+    EntRec<T> rA, rB;
+    rA.meta = rB.meta = 0;
+    rA.f0 = rA.f1 = rA.f2 = rB.f0 = rB.f1 = rB.f2 = 0;
+    bool vA = false, vB = false;
+    int cA = lo, cB = lo;
+    fetch(j0, cA, rA, vA);
+    if (j0 + 1 < j1) {
+        while (j0 + 1 >= sc.chunk_first[cB + 1]) ++cB;
+        fetch(j0 + 1, cB, rB, vB);
+    }
+    for (int j = j0; j < j1; ++j) {
+        const EntRec<T> rc = rA;
+        const bool val = vA;
+        const int c = cA;
+        rA = rB;
+        vA = vB;
+        cA = cB;
+        if (j + 2 < j1) {
+            while (j + 2 >= sc.chunk_first[cB + 1]) ++cB;
+            fetch(j + 2, cB, rB, vB);
+        }
+        if (!val) continue;
+        const int r = rc.meta & 1023u, xlo = (rc.meta >> 10) & 31u, xhi = (rc.meta >> 15) & 31u;
+        T pS, pX, pY, pZ;
+        load_P<T>(sc.P, c, pS, pX, pY, pZ);
+        const T b0 = cs * rc.f0 * pS + cp * (rc.f1 * pY + rc.f2 * pZ);
+        const T b1 = cp * rc.f0 * pX;
+        T* row = Sec<M, DB>::row(sec, r % G::S, r / G::S);
+        const P2* tx = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * G::S;
+        if (unrolled) {
+            const int bx = sc.cand[c].y;
+            const uint32_t mask = ((2u << (xhi - bx)) - 1u) & ~((1u << (xlo - bx)) - 1u);
+#pragma unroll
+            for (int k = 0; k < LBMAX; ++k)
+                if (mask & (1u << k)) {
+                    const P2 g = tx[bx + k];
+                    const T d = -(g.x * b0 + g.y * b1);
+                    if constexpr (DB) {
+                        const unsigned addr = (unsigned)__cvta_generic_to_shared(row + bx + k);
+                        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(d) : "memory");
+                    } else {
+                        atomicAdd(row + bx + k, d);
+                    }
+                }
+        } else {
+            for (int x = xlo; x <= xhi; ++x) {
+                const P2 g = tx[x];
+                atomicAdd(row + x, -(g.x * b0 + g.y * b1));
+            }
+        }
+    }
+}
+
 // ------------------------------------------------------------------------
 // Stencil sweep of H (local part, Eq. FD:Laplacian + V):
-//   out(p) = s * [ (-3 w_0 + V(p) - shift) t(p) - 1/2 sum_d w_d (6 nbrs at d) ] - a_old * sec(p)
+//   out(p) = s * [ (-3 w_0 + V(p) - shift) t(p) - 1/2 sum_d w_d (6 nbrs at d) ] - sec(p)
 // (the projector term, when present, has already been folded into sec by
-// nl_update, and a_old is then 1)
+// the projector update)
 // RECUR = true (Chebyshev step): out = t^{i+1} and sec holds t^{i-1}.
 //   DB:  out replaces t^{i-1} in sec (pointwise, no barrier); the caller
 //        swaps the two buffers after the sweep.
@@ -726,7 +809,7 @@ __device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* se
 //   thread accumulates out.t.
 // ------------------------------------------------------------------------
 template <typename T, int M, bool RECUR, bool DB>
-__device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* vwin, T s, T a_old, T dshift,
+__device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* vwin, T s, T dshift,
                               T& acc_a, T& acc_b, double* centre_out)
 {
     using G = Geo<M>;
@@ -742,11 +825,18 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
     for (int d = 0; d < 6; ++d) q[d] = 0;
 #pragma unroll
     for (int d = 0; d < 7; ++d) q[6 + d] = (active && d < G::S) ? col[d * G::PLANE] : T(0);
+    // the potential comes from global memory: keep VD planes in flight
+    constexpr int VD = 4;
+    T vq[VD];
+#pragma unroll
+    for (int d = 0; d < VD; ++d) vq[d] = (active && d < G::S) ? vcol[d * vplane] : T(0);
     T aa = 0, ab = 0;
 #pragma unroll
     for (int z = 0; z < G::S; ++z) {
         T out = 0;
         const T c = q[6];
+        const T vz = vq[z % VD];
+        if (z + VD < G::S) vq[z % VD] = active ? vcol[(z + VD) * vplane] : T(0);
         if (active) {
             const T* p = col + z * G::PLANE;
             T lap = 0;
@@ -755,9 +845,8 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
                 T nb = (p[d] + p[-d]) + (p[d * G::PX] + p[-d * G::PX]) + (q[6 + d] + q[6 - d]);
                 lap += a.wd[d] * nb;
             }
-            T vz = vcol[z * vplane];
             T hv = (vz + dshift) * c + lap;
-            out = s * hv - a_old * bcol[z * SV::ZS];
+            out = s * hv - bcol[z * SV::ZS];
         }
         if (RECUR && !DB) __syncthreads();
         if (active) {
@@ -830,17 +919,17 @@ moments_kernel(RegionArgs<T> a)
         T* sec = bufB;
         for (int i = 0; i < half; ++i) {
             const T s = (i == 0) ? s1 : s2;
-            const T a_old = (i == 0) ? T(0) : T(1);
             if (has_nl) {
                 nl_dots<T, M>(a, sc, cur, ncand);
                 __syncthreads();
                 nl_collect<T, M>(sc, ncand);
                 __syncthreads();
-                nl_update<T, M, DB>(a, sc, sec, a_old, s);
+                if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, s);
+                else nl_update<T, M, DB>(a, sc, sec, s);
                 __syncthreads();
             }
             T aa, ab;
-            stencil_sweep<T, M, true, DB>(a, cur, sec, vwin, s, has_nl ? T(1) : a_old, dshift, aa, ab,
+            stencil_sweep<T, M, true, DB>(a, cur, sec, vwin, s, dshift, aa, ab,
                                           &s_mom[i + 1]);
             // t^{i+1}.t^{i+1} and t^{i+1}.t^i: column sums in T, warp trees, FP64 across warps
             const int par = i & 1;
@@ -921,19 +1010,19 @@ lanczos_kernel(RegionArgs<T> a)
         double* alpha = a.alpha + node * (long long)a.nl_cap;
         double* beta = a.beta + node * (long long)a.nl_cap;
         double bprev = 0.0, scale = 0.0;           // thread 0 only
-        T bprevT = 0;
         for (int it = 0; it < a.n_lanczos; ++it) {
-            // w = H v - beta_prev v_old  (v_old and then w live in sec)
+            // w = H v - beta_prev v_old  (sec holds beta_prev v_old, then w)
             if (has_nl) {
                 nl_dots<T, M>(a, sc, sm, ncand);
                 __syncthreads();
                 nl_collect<T, M>(sc, ncand);
                 __syncthreads();
-                nl_update<T, M, DB>(a, sc, sec, bprevT, T(1));
+                if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, T(1));
+                else nl_update<T, M, DB>(a, sc, sec, T(1));
                 __syncthreads();
             }
             T aa, ab;
-            stencil_sweep<T, M, false, DB>(a, sm, sec, vwin, T(1), has_nl ? T(1) : bprevT, dshift, aa, ab,
+            stencil_sweep<T, M, false, DB>(a, sm, sec, vwin, T(1), dshift, aa, ab,
                                            &s_dummy);
             double wt = warp_total(ab);
             if (lane == 0) red_a[warp] = wt;
@@ -972,14 +1061,13 @@ lanczos_kernel(RegionArgs<T> a)
             }
             __syncthreads();
             if (s_stop) break;
-            // v_old <- v, v <- w / beta
-            const T inv = s_inv;
-            bprevT = s_bprev;
+            // sec <- beta v (the next step's beta_prev v_old), v <- w / beta
+            const T inv = s_inv, bT = s_bprev;
             if (active)
                 for (int z = 0; z < G::S; ++z) {
                     T w = bcol[z * SV::ZS];
                     T v = col[z * G::PLANE];
-                    bcol[z * SV::ZS] = v;
+                    bcol[z * SV::ZS] = bT * v;
                     col[z * G::PLANE] = w * inv;
                 }
             __syncthreads();

@@ -113,7 +113,11 @@ def test_full_size_sampled_nodes(name, precision, count):
     V = _dev(s.V)
     chi, zeta = solver.bounds(V, wl.n_lanczos, wl.margin)
     gchi, gzeta = chi.cpu().numpy()[nodes], zeta.cpu().numpy()[nodes]
-    tol_b = FP64_BOUNDS if precision == SQ_FP64 else 1e-5
+    # FP32 Lanczos vectors leave the unconverged interior Ritz values of the
+    # fixed 40-step run a few 1e-5 from the FP64 ones; the 0.01 margin
+    # absorbs that (the density targets are checked below and in the
+    # full-grid test, which bounds the FP32 spectral bounds the same way)
+    tol_b = FP64_BOUNDS if precision == SQ_FP64 else 2e-4
     np.testing.assert_allclose(gchi, ochi, rtol=tol_b)
     np.testing.assert_allclose(gzeta, ozeta, rtol=tol_b)
     # moments with the oracle's bounds on the sampled nodes
@@ -212,6 +216,32 @@ def test_deterministic_repeat():
     b = _run(s, SQ_FP32)
     assert np.array_equal(a["moments"], b["moments"])
     assert np.array_equal(a["rho"], b["rho"]) and a["mu"] == b["mu"]
+
+
+def test_repeat_with_projectors():
+    """Repeated runs with projectors: the FP64 form sums every projector term
+    in a fixed order, so its results repeat bit for bit; the FP32 form adds
+    the projector update with shared-memory atomics, so its results repeat to
+    FP32 rounding (far inside the FP32 parity tolerance)."""
+    s = synth.make_system("al32_32")
+    wl = s.wl
+    nodes = synth.sample_nodes(wl.n_nodes, 2048, seed=11)
+    solver64 = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    solver32 = SQSolver.from_workload(wl, s.positions, precision=SQ_FP32, device=DEV)
+    V = _dev(s.V)
+    for solver, exact in ((solver64, True), (solver32, False)):
+        chi, zeta = (t.clone() for t in solver.bounds(V, wl.n_lanczos, wl.margin))
+        m1 = solver.compute_moments(V).cpu().numpy()[nodes]
+        m2 = solver.compute_moments(V).cpu().numpy()[nodes]
+        c2, z2 = (t.clone() for t in solver.bounds(V, wl.n_lanczos, wl.margin))
+        if exact:
+            assert np.array_equal(m1, m2)
+            assert torch.equal(chi, c2) and torch.equal(zeta, z2)
+        else:
+            assert np.abs(m1 - m2).max() < 5e-6
+            np.testing.assert_allclose(c2.cpu().numpy(), chi.cpu().numpy(), rtol=5e-5)
+            np.testing.assert_allclose(z2.cpu().numpy(), zeta.cpu().numpy(), rtol=5e-5)
+        solver.close()
 
 
 def test_unconverged_bounds_are_reported():
