@@ -381,12 +381,119 @@ def run_gb300(a):
         dist.destroy_process_group()
 
 
+def run_batch(a):
+    """16 uneven seeded systems (synth.batch_workloads) as one CUDA-graph
+    launch per step (sq_batch_*), FP32; the same metric summed over the
+    systems, and the same systems run one after another through the
+    single-system calls for comparison."""
+    import torch
+    from paper_1708_07913_gb300 import SQ_FP32, SQBatch, SQSolver, build
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    build()
+    wls = synth.batch_workloads()
+    systems = [synth.make_system(w) for w in wls]
+    margin, n_lz = wls[0].margin, wls[0].n_lanczos
+    Vh = [torch.from_numpy(s.V.ravel().copy()).pin_memory() for s in systems]
+    Vs = [v.to(dev) for v in Vh]
+    solvers = [SQSolver.from_workload(s.wl, s.positions, precision=SQ_FP32, device=str(dev)) for s in systems]
+    Ne, kT = [w.n_electrons for w in wls], [w.kT for w in wls]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # sequential reference: the single-system calls, one system after another
+    def seq():
+        for s, sv, V in zip(systems, solvers, Vs):
+            sv.solve(V, s.wl.n_electrons, s.wl.kT, n_lz, margin)
+    seq()
+    flush.fill_(1.0)
+    e0, e1 = ev(), ev()
+    e0.record(stream)
+    seq()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_seq = e0.elapsed_time(e1) / 1e3
+    batch = SQBatch(solvers)
+    t0 = time.perf_counter()
+    batch.run(Vs, Ne, kT, n_lz, margin)                      # first call: autotune + capture
+    batch.results()
+    t_tune = time.perf_counter() - t0
+    for _ in range(a.warmup):
+        batch.run(Vs, Ne, kT, n_lz, margin)
+        batch.results()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times = []
+    for _ in range(a.steps):
+        flush.fill_(1.0)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        batch.run(Vs, Ne, kT, n_lz, margin)
+        e1.record(stream)
+        batch.results()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    e2e = []
+    for _ in range(max(2, a.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for v, vh in zip(Vs, Vh):
+            v.copy_(vh, non_blocking=True)
+        batch.run(Vs, Ne, kT, n_lz, margin)
+        batch.results()
+        rho_h = [sv.rho.to("cpu", non_blocking=True) for sv in solvers]
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    t = float(np.mean(times))
+    units = sum(w.n_nodes * w.npl for w in wls)
+    flops = sum(flops_moments(w) + flops_lanczos(w) for w in wls)
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # kernels per system in one graph: potential copy, Lanczos, tridiagonal extremes, moments, weights,
+    # Fermi-state init, bracket, two end counts and 201 bisection counts, density
+    per_graph = len(wls) * (1 + 1 + 1 + 1 + 1 + 1 + 1 + 2 + 201 + 1)
+    line = {
+        "metric": METRIC, "value": units / t, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (16 seeded FCC Al-like crystals, Gaussian V and KB projectors)",
+        "config": {"workload": "batch16: " + "; ".join(
+            f"{w.cells}^3 cells {w.n}^3 grid h={w.h:.3f} {2 * w.m + 1}^3 regions n_pl={w.npl} kT={w.kT:.3f}"
+            for w in wls),
+            "precision": "FP32 recurrence/Lanczos vectors, FP64 moments, weights, Fermi level, energies",
+            "n_lanczos": n_lz, "margin": margin, "launch": "one CUDA graph per step, one stream per system",
+            "l2": "flushed between timed steps (256 MB write)", "parallelism": "single GPU"},
+        "sequential_s": t_seq, "batch_speedup_vs_sequential": t_seq / t, "autotune_first_call_s": t_tune,
+        "blocks_per_system": batch.blocks(),
+        "roofline": {"kernel": "all region kernels of the batch", "bound": "alu", "achieved": flops / t / 1e12,
+                     "peak": peak, "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                     "peak_basis": f"FP32 CUDA-core pipe at {sm_max:.0f} MHz x {sms} SMs"},
+        "e2e": {"value": units / float(np.median(e2e)), "unit": UNIT,
+                "h2d_bytes_per_step": sum(w.n_nodes * 8 for w in wls),
+                "d2h_bytes_per_step": sum(w.n_nodes * 8 + 4 * 8 for w in wls)},
+        "gpu_launches": per_graph * a.steps,
+        "graph_launches": a.steps,
+        "clocks": clk,
+        "cpu_baseline": {"value": None, "unit": UNIT, "cores": 0, "kind": "oracle",
+                         "sample": "not timed for the batch (see the single-workload line)"},
+    }
+    batch.close()
+    for sv in solvers:
+        sv.close()
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.warmup < 3:
         a.warmup = 3
     if a.impl == "reference":
         run_reference(a)
+    elif a.workload == "batch16":
+        run_batch(a)
     else:
         run_gb300(a)
 

@@ -174,6 +174,52 @@ int sq_density_energy_noalloc(int n1, int n2, int n3, double h, int npl,
                               double *e_band_host, double *e_ent_host, double *n_elec_host,
                               void *cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Batch of independent systems.  The paper treats one system at a time (its
+ * parallelism is over the nodes of one grid, Section 3.2); it has no
+ * counterpart for this.  A batch runs the whole step of the path -- spectral
+ * bounds, moments, Fermi level and density/energies, as the single-system
+ * calls above define them -- for every context in it as ONE CUDA graph
+ * launch, each system on its own stream, so that systems of uneven size,
+ * region and temperature share the GPU and the launch-bound Fermi-level
+ * bisections of the systems overlap.
+ *
+ * sq_batch_create(out, n, ctxs, cuda_stream)
+ *   ctxs: HOST array of n >= 1 contexts, not owned (they must outlive the
+ *   batch and must not be used elsewhere while a batch run is in flight).
+ *   cuda_stream: the caller's stream (NULL = legacy default stream); batch
+ *   runs start after work already enqueued on it, and work enqueued on it
+ *   afterwards starts after the batch.  Creates one stream per system.
+ * sq_batch_run(b, V, chi, zeta, moments, rho, n_electrons, kT, n_lanczos,
+ *              margin)
+ *   V, chi, zeta, moments, rho: HOST arrays of n DEVICE pointers, each with
+ *   the layout of the single-system calls; n_electrons, kT: HOST arrays of n.
+ *   Enqueues the step of every system and returns without waiting.  The
+ *   first call tunes the launch (and so takes about two extra batch steps):
+ *   two plans are timed as whole graphs -- every region kernel on its full
+ *   persistent grid, and grids cut to SM shares proportional to each
+ *   system's work (nodes x region points x steps) -- and the faster is kept.  A call whose pointers or parameters differ from
+ *   the previous call's re-captures the graph (same plan).  Argument errors
+ *   are SQ_EINVAL (checked on the host before anything is enqueued).
+ * sq_batch_results(b, mu, e_band, e_ent, n_elec)
+ *   Waits for the last run; HOST arrays of n (each may be NULL) receive each
+ *   system's Fermi level, band energy, entropy energy and electron count
+ *   (rho etc. are in the device arrays given to sq_batch_run).  Returns the
+ *   first error of any system (SQ_ENOCONV, a latched device error, ...).
+ * sq_batch_blocks(b, blocks): HOST array of n: the region-kernel grid chosen
+ *   per system (0 = the full persistent grid); SQ_EINVAL before the first run.
+ * sq_batch_destroy(b): releases the batch's streams and graph (NULL: no-op).
+ * ------------------------------------------------------------------------- */
+typedef struct sq_batch sq_batch;
+int sq_batch_create(sq_batch **out, int n, sq_ctx *const *ctxs, void *cuda_stream);
+int sq_batch_run(sq_batch *b, const double *const *V, double *const *chi, double *const *zeta,
+                 double *const *moments, double *const *rho, const double *n_electrons,
+                 const double *kT, int n_lanczos, double margin);
+int sq_batch_results(sq_batch *b, double *mu_host, double *e_band_host, double *e_ent_host,
+                     double *n_elec_host);
+int sq_batch_blocks(const sq_batch *b, int *blocks_host);
+void sq_batch_destroy(sq_batch *b);
+
 /* Wait for the context's stream and return any latched device error. */
 int sq_sync(sq_ctx *ctx);
 

@@ -13,7 +13,7 @@ from __future__ import annotations
 from . import sq
 from .sq import SQ_FP32, SQ_FP64, SQError
 
-__all__ = ["sq", "SQSolver", "SQ_FP32", "SQ_FP64", "SQError", "build"]
+__all__ = ["sq", "SQSolver", "SQBatch", "SQ_FP32", "SQ_FP64", "SQError", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -97,3 +97,40 @@ class SQSolver:
     @property
     def launches(self):
         return sq.sq_launch_count(self.ctx)
+
+
+class SQBatch:
+    """Several SQSolver systems run as one batch: the whole step (bounds,
+    moments, Fermi level, density/energies) of every system is one CUDA graph
+    launch, each system on its own stream (sq_batch_* in include/sq.h).
+    Results land in each solver's own buffers (chi, zeta, moments, rho)."""
+
+    def __init__(self, solvers):
+        self.solvers = list(solvers)
+        self.batch = sq.sq_batch_create([s.ctx for s in self.solvers])
+
+    def run(self, V, n_electrons, kT, n_lanczos=40, margin=0.01):
+        """Enqueue the step for every system (V: list of device tensors)."""
+        S = self.solvers
+        sq.sq_batch_run(self.batch, list(V), [s.chi for s in S], [s.zeta for s in S], [s.moments for s in S],
+                        [s.rho for s in S], list(n_electrons), list(kT), n_lanczos, margin)
+
+    def results(self):
+        """Wait; per system a dict with mu, e_band, e_ent, n_elec."""
+        mu, eb, es, ne = sq.sq_batch_results(self.batch, len(self.solvers))
+        return [dict(mu=a, e_band=b, e_ent=c, n_elec=d) for a, b, c, d in zip(mu, eb, es, ne)]
+
+    def blocks(self):
+        """Region-kernel grid chosen per system by the autotuner (0 = the full persistent grid)."""
+        return sq.sq_batch_blocks(self.batch, len(self.solvers))
+
+    def close(self):
+        if getattr(self, "batch", None):
+            sq.sq_batch_destroy(self.batch)
+            self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

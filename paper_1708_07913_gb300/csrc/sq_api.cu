@@ -271,6 +271,228 @@ int region_blocks(sq_ctx* c, int which, int* blocks)
     return SQ_OK;
 }
 
+// Lanczos coefficient buffers for n_lanczos steps (allocated outside any
+// stream capture).
+int ensure_lanczos_buffers(sq_ctx* c, int n_lanczos)
+{
+    if (n_lanczos <= c->nl_cap) return SQ_OK;
+    if (c->d_alpha) cudaFree(c->d_alpha);
+    if (c->d_beta) cudaFree(c->d_beta);
+    if (c->d_klen) cudaFree(c->d_klen);
+    c->d_alpha = c->d_beta = nullptr;
+    c->d_klen = nullptr;
+    c->nl_cap = 0;
+    int rc;
+    if ((rc = dev_alloc(&c->d_alpha, sizeof(double) * c->g.Nd * n_lanczos)) ||
+        (rc = dev_alloc(&c->d_beta, sizeof(double) * c->g.Nd * n_lanczos)) ||
+        (rc = dev_alloc(&c->d_klen, sizeof(int) * c->g.Nd)))
+        return rc;
+    c->nl_cap = n_lanczos;
+    return SQ_OK;
+}
+
+// Lanczos kernel on `blocks` CTAs, then the tridiagonal extremes (Vp built).
+int enqueue_bounds(sq_ctx* c, int blocks, int n_lanczos, double margin, double* chi, double* zeta)
+{
+    int rc;
+    if (c->precision == SQ_FP32) {
+        RegionArgs<float> a = region_args<float>(c);
+        a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
+        rc = region_launch_f32(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
+    } else {
+        RegionArgs<double> a = region_args<double>(c);
+        a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
+        rc = region_launch_f64(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
+    }
+    c->launches++;
+    if (rc) return rc;
+    return launch_tridiag_bounds(c, margin, chi, zeta);
+}
+
+// Moments kernel on `blocks` CTAs (Vp built).
+int enqueue_moments(sq_ctx* c, int blocks, const double* chi, const double* zeta, double* moments)
+{
+    int rc;
+    if (c->precision == SQ_FP32) {
+        RegionArgs<float> a = region_args<float>(c);
+        a.chi = chi; a.zeta = zeta; a.moments = moments;
+        rc = region_launch_f32(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
+    } else {
+        RegionArgs<double> a = region_args<double>(c);
+        a.chi = chi; a.zeta = zeta; a.moments = moments;
+        rc = region_launch_f64(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
+    }
+    c->launches++;
+    return rc;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------
+// Batch of independent systems: the whole SCF-iteration step of every
+// context as one CUDA graph, one forked stream per system.
+// ------------------------------------------------------------------------
+struct sq_batch {
+    int n = 0;
+    std::vector<sq_ctx*> ctx;
+    cudaStream_t stream = nullptr;               // the caller's stream (may be the legacy stream)
+    cudaStream_t own = nullptr;                  // the batch's stream: captures and launches (owned)
+    std::vector<cudaStream_t> st;                // one per system (owned)
+    cudaEvent_t fork = nullptr, ev_in = nullptr, ev_out = nullptr;
+    std::vector<cudaEvent_t> join;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<int> blocks;                     // region-kernel grid per system (0: the default)
+    bool tuned = false;
+    // arguments the instantiated graph was captured with
+    std::vector<const void*> key_ptr;
+    std::vector<double> key_val;
+    int key_nl = 0;
+    double key_margin = -1.0;
+    std::vector<double> state;                   // host copy of the Fermi/energy states
+};
+
+namespace {
+
+void batch_free_graph(sq_batch* b)
+{
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    b->exec = nullptr;
+}
+
+struct BatchArgs {
+    const double* const* V;
+    double* const* chi;
+    double* const* zeta;
+    double* const* moments;
+    double* const* rho;
+    const double* Ne;
+    const double* kT;
+    int n_lanczos;
+    double margin;
+};
+
+// Enqueue the whole step of system i on the current stream of its context
+// (bl, bm: grids of the Lanczos and moments kernels).
+int batch_enqueue_one(sq_batch* b, int i, const BatchArgs& A, int bl, int bm)
+{
+    sq_ctx* c = b->ctx[i];
+    int rc;
+    if ((rc = launch_build_vpad(c, A.V[i]))) return rc;
+    if ((rc = enqueue_bounds(c, bl, A.n_lanczos, A.margin, A.chi[i], A.zeta[i]))) return rc;
+    if ((rc = enqueue_moments(c, bm, A.chi[i], A.zeta[i], A.moments[i]))) return rc;
+    if ((rc = launch_weights(c, A.moments[i]))) return rc;
+    if ((rc = enqueue_fermi(c, A.chi[i], A.zeta[i], A.Ne[i], A.kT[i]))) return rc;
+    return enqueue_density(c, A.chi[i], A.zeta[i], 0.0, A.kT[i], A.rho[i], 1);
+}
+
+// Capture every system's step, each on its own stream forked from and
+// joined back into b->stream, and instantiate the graph.
+int batch_capture(sq_batch* b, const BatchArgs& A, const std::vector<int>& blocks, cudaGraphExec_t* out)
+{
+    // grids first: nothing but stream work happens inside the capture
+    std::vector<int> bl(b->n), bm(b->n);
+    for (int i = 0; i < b->n; ++i) {
+        int rc;
+        if ((rc = region_blocks(b->ctx[i], 1, &bl[i])) || (rc = region_blocks(b->ctx[i], 0, &bm[i]))) return rc;
+        if (blocks[i] > 0) {
+            bl[i] = std::min(bl[i], blocks[i]);
+            bm[i] = std::min(bm[i], blocks[i]);
+        }
+    }
+    std::vector<cudaStream_t> saved(b->n);
+    for (int i = 0; i < b->n; ++i) saved[i] = b->ctx[i]->stream;
+    if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return SQ_ECUDA;
+    }
+    int rc = SQ_OK;
+    if (cudaEventRecord(b->fork, b->own) != cudaSuccess) rc = SQ_ECUDA;
+    for (int i = 0; i < b->n && rc == SQ_OK; ++i) {
+        b->ctx[i]->stream = b->st[i];
+        if (cudaStreamWaitEvent(b->st[i], b->fork, 0) != cudaSuccess) { rc = SQ_ECUDA; break; }
+        rc = batch_enqueue_one(b, i, A, bl[i], bm[i]);
+        if (rc) break;
+        if (cudaEventRecord(b->join[i], b->st[i]) != cudaSuccess ||
+            cudaStreamWaitEvent(b->own, b->join[i], 0) != cudaSuccess)
+            rc = SQ_ECUDA;
+    }
+    for (int i = 0; i < b->n; ++i) b->ctx[i]->stream = saved[i];
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->own, &graph);
+    if (rc == SQ_OK && e != cudaSuccess) rc = SQ_ECUDA;
+    if (rc == SQ_OK && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) rc = SQ_ECUDA;
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
+// Time one launch of an instantiated graph.
+int batch_time(sq_batch* b, cudaGraphExec_t g, float* ms)
+{
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return SQ_ECUDA;
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return SQ_ECUDA; }
+    int rc = SQ_OK;
+    if (cudaEventRecord(e0, b->own) != cudaSuccess || cudaGraphLaunch(g, b->own) != cudaSuccess ||
+        cudaEventRecord(e1, b->own) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+        cudaEventElapsedTime(ms, e0, e1) != cudaSuccess)
+        rc = SQ_ECUDA;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+// The autotuner.  Two launch plans are timed as complete graphs: every
+// region kernel on its full persistent grid (the systems' region kernels
+// queue for the SMs, and the small Fermi and density launches of a finished
+// system overlap the next), and grids cut to SM shares proportional to each
+// system's work (all systems side by side); the faster plan is kept.  Work
+// per system = nodes x region points x (n_lanczos + n_pl/2) x (1 + the
+// projector share of a point's arithmetic).
+int batch_tune(sq_batch* b, const BatchArgs& A)
+{
+    const int n = b->n;
+    std::vector<double> w(n, 0.0);
+    double W = 0.0;
+    for (int i = 0; i < n; ++i) {
+        const sq_ctx* c = b->ctx[i];
+        const double S = 2.0 * c->g.m + 1.0;
+        // projector supports covering a point (atom density x support volume),
+        // at ~8 flops each against ~52 for the local stencil
+        const double cell = (double)c->g.Nd * c->g.h * c->g.h * c->g.h;
+        const double pairs = (c->has_s || c->has_p) ? c->n_atoms * (4.0 / 3.0) * M_PI * c->rnl * c->rnl * c->rnl / cell
+                                                    : 0.0;
+        w[i] = (double)c->g.Nd * S * S * S * (A.n_lanczos + c->npl / 2) * (1.0 + pairs * 8.0 / 52.0);
+        W += w[i];
+    }
+    std::vector<int> full(n, 0), share(n, 1);
+    for (int i = 0; i < n; ++i) {
+        int bm = 0;
+        int rc = region_blocks(b->ctx[i], 0, &bm);
+        if (rc) return rc;
+        const int per_sm = std::max(1, bm / std::max(1, b->ctx[i]->sm_count));
+        share[i] = std::max(1, (int)std::floor(w[i] / W * b->ctx[i]->sm_count * per_sm));
+    }
+    float best = 0.f;
+    std::vector<int> pick = full;
+    for (int plan = 0; plan < 2; ++plan) {
+        const std::vector<int>& bl = plan == 0 ? full : share;
+        cudaGraphExec_t g = nullptr;
+        int rc = batch_capture(b, A, bl, &g);
+        float ms = 0.f;
+        if (rc == SQ_OK) rc = batch_time(b, g, &ms);
+        if (g) cudaGraphExecDestroy(g);
+        if (rc) return rc;
+        if (plan == 0 || ms < best) {
+            best = ms;
+            pick = bl;
+        }
+    }
+    b->blocks = pick;
+    b->tuned = true;
+    return SQ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -402,36 +624,12 @@ int sq_spectral_bounds(sq_ctx* c, const double* V, double* chi, double* zeta, in
     if (!c || n_lanczos < 1 || n_lanczos > 512 || !is_fin(margin) || margin < 0.0 || margin >= 1.0)
         return SQ_EINVAL;
     if (!is_device_ptr(V) || !is_device_ptr(chi) || !is_device_ptr(zeta)) return SQ_EINVAL;
-    if (n_lanczos > c->nl_cap) {
-        if (c->d_alpha) cudaFree(c->d_alpha);
-        if (c->d_beta) cudaFree(c->d_beta);
-        if (c->d_klen) cudaFree(c->d_klen);
-        c->d_alpha = c->d_beta = nullptr;
-        c->d_klen = nullptr;
-        c->nl_cap = 0;
-        int rc;
-        if ((rc = dev_alloc(&c->d_alpha, sizeof(double) * c->g.Nd * n_lanczos)) ||
-            (rc = dev_alloc(&c->d_beta, sizeof(double) * c->g.Nd * n_lanczos)) ||
-            (rc = dev_alloc(&c->d_klen, sizeof(int) * c->g.Nd)))
-            return rc;
-        c->nl_cap = n_lanczos;
-    }
-    int rc = launch_build_vpad(c, V);
+    int rc = ensure_lanczos_buffers(c, n_lanczos);
     if (rc) return rc;
+    if ((rc = launch_build_vpad(c, V))) return rc;
     int blocks = 0;
     if ((rc = region_blocks(c, 1, &blocks))) return rc;
-    if (c->precision == SQ_FP32) {
-        RegionArgs<float> a = region_args<float>(c);
-        a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
-        rc = region_launch_f32(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
-    } else {
-        RegionArgs<double> a = region_args<double>(c);
-        a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
-        rc = region_launch_f64(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
-    }
-    c->launches++;
-    if (rc) return rc;
-    return launch_tridiag_bounds(c, margin, chi, zeta);
+    return enqueue_bounds(c, blocks, n_lanczos, margin, chi, zeta);
 }
 
 int sq_moments(sq_ctx* c, const double* V, const double* chi, const double* zeta, double* moments)
@@ -443,17 +641,7 @@ int sq_moments(sq_ctx* c, const double* V, const double* chi, const double* zeta
     if (rc) return rc;
     int blocks = 0;
     if ((rc = region_blocks(c, 0, &blocks))) return rc;
-    if (c->precision == SQ_FP32) {
-        RegionArgs<float> a = region_args<float>(c);
-        a.chi = chi; a.zeta = zeta; a.moments = moments;
-        rc = region_launch_f32(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
-    } else {
-        RegionArgs<double> a = region_args<double>(c);
-        a.chi = chi; a.zeta = zeta; a.moments = moments;
-        rc = region_launch_f64(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
-    }
-    c->launches++;
-    return rc;
+    return enqueue_moments(c, blocks, chi, zeta, moments);
 }
 
 int sq_fermi_level(sq_ctx* c, const double* moments, const double* chi, const double* zeta, double n_electrons,
@@ -501,6 +689,139 @@ void sq_destroy(sq_ctx* c)
     if (!c) return;
     cudaStreamSynchronize(c->stream);
     free_ctx(c);
+}
+
+int sq_batch_create(sq_batch** out, int n, sq_ctx* const* ctxs, void* cuda_stream)
+{
+    if (!out) return SQ_EINVAL;
+    *out = nullptr;
+    if (n < 1 || n > 4096 || !ctxs) return SQ_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!ctxs[i]) return SQ_EINVAL;
+    sq_batch* b = new (std::nothrow) sq_batch();
+    if (!b) return SQ_ENOMEM;
+    b->n = n;
+    b->ctx.assign(ctxs, ctxs + n);
+    b->stream = (cudaStream_t)cuda_stream;
+    b->st.assign(n, nullptr);
+    b->join.assign(n, nullptr);
+    b->blocks.assign(n, 0);
+    b->state.assign((size_t)n * FERMI_STATE, 0.0);
+    int rc = SQ_OK;
+    if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking) != cudaSuccess)
+        rc = SQ_ECUDA;
+    for (int i = 0; i < n && rc == SQ_OK; ++i)
+        if (cudaStreamCreateWithFlags(&b->st[i], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&b->join[i], cudaEventDisableTiming) != cudaSuccess)
+            rc = SQ_ECUDA;
+    if (rc) {
+        cudaGetLastError();
+        sq_batch_destroy(b);
+        return rc;
+    }
+    *out = b;
+    return SQ_OK;
+}
+
+int sq_batch_run(sq_batch* b, const double* const* V, double* const* chi, double* const* zeta,
+                 double* const* moments, double* const* rho, const double* n_electrons, const double* kT,
+                 int n_lanczos, double margin)
+{
+    if (!b || !V || !chi || !zeta || !moments || !rho || !n_electrons || !kT) return SQ_EINVAL;
+    if (n_lanczos < 1 || n_lanczos > 512 || !is_fin(margin) || margin < 0.0 || margin >= 1.0) return SQ_EINVAL;
+    std::vector<const void*> key;
+    std::vector<double> kv;
+    for (int i = 0; i < b->n; ++i) {
+        sq_ctx* c = b->ctx[i];
+        if (!is_device_ptr(V[i]) || !is_device_ptr(chi[i]) || !is_device_ptr(zeta[i]) ||
+            !is_device_ptr(moments[i]) || !is_device_ptr(rho[i]))
+            return SQ_EINVAL;
+        if (!is_fin(kT[i]) || kT[i] <= 0.0 || !is_fin(n_electrons[i]) || n_electrons[i] <= 0.0 ||
+            n_electrons[i] >= 2.0 * (double)c->g.Nd)
+            return SQ_EINVAL;
+        int rc = ensure_lanczos_buffers(c, n_lanczos);
+        if (rc) return rc;
+        key.insert(key.end(), {V[i], chi[i], zeta[i], moments[i], rho[i]});
+        kv.insert(kv.end(), {n_electrons[i], kT[i]});
+    }
+    BatchArgs A = {V, chi, zeta, moments, rho, n_electrons, kT, n_lanczos, margin};
+    // the batch's stream follows the caller's (inputs written there are ready)
+    if (cudaEventRecord(b->ev_in, b->stream) != cudaSuccess || cudaStreamWaitEvent(b->own, b->ev_in, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return SQ_ECUDA;
+    }
+    const bool same = b->exec && key == b->key_ptr && kv == b->key_val && n_lanczos == b->key_nl &&
+                      margin == b->key_margin;
+    if (!same) {
+        batch_free_graph(b);
+        int rc = SQ_OK;
+        if (!b->tuned) rc = batch_tune(b, A);
+        if (rc == SQ_OK) rc = batch_capture(b, A, b->blocks, &b->exec);
+        if (rc) {
+            b->exec = nullptr;
+            return rc;
+        }
+        b->key_ptr = key;
+        b->key_val = kv;
+        b->key_nl = n_lanczos;
+        b->key_margin = margin;
+    }
+    if (cudaGraphLaunch(b->exec, b->own) != cudaSuccess || cudaEventRecord(b->ev_out, b->own) != cudaSuccess ||
+        cudaStreamWaitEvent(b->stream, b->ev_out, 0) != cudaSuccess) {    // and the caller's follows the batch
+        cudaGetLastError();
+        return SQ_ECUDA;
+    }
+    for (sq_ctx* c : b->ctx) c->launches++;
+    return SQ_OK;
+}
+
+int sq_batch_results(sq_batch* b, double* mu_host, double* e_band_host, double* e_ent_host, double* n_elec_host)
+{
+    if (!b) return SQ_EINVAL;
+    for (int i = 0; i < b->n; ++i)
+        if (cudaMemcpyAsync(b->state.data() + (size_t)i * FERMI_STATE, b->ctx[i]->d_fermi,
+                            sizeof(double) * FERMI_STATE, cudaMemcpyDeviceToHost, b->own) != cudaSuccess) {
+            cudaGetLastError();
+            return SQ_ECUDA;
+        }
+    if (cudaStreamSynchronize(b->own) != cudaSuccess) {
+        cudaGetLastError();
+        return SQ_ECUDA;
+    }
+    int first = SQ_OK;
+    for (int i = 0; i < b->n; ++i) {
+        int e = take_device_error(b->ctx[i]);
+        int r = fermi_result(b->state.data() + (size_t)i * FERMI_STATE, mu_host ? mu_host + i : nullptr,
+                             e_band_host ? e_band_host + i : nullptr, e_ent_host ? e_ent_host + i : nullptr,
+                             n_elec_host ? n_elec_host + i : nullptr);
+        if (!first) first = e ? e : r;
+    }
+    return first;
+}
+
+int sq_batch_blocks(const sq_batch* b, int* blocks_host)
+{
+    if (!b || !blocks_host) return SQ_EINVAL;
+    for (int i = 0; i < b->n; ++i) blocks_host[i] = b->blocks[i];
+    return b->tuned ? SQ_OK : SQ_EINVAL;
+}
+
+void sq_batch_destroy(sq_batch* b)
+{
+    if (!b) return;
+    batch_free_graph(b);
+    for (cudaStream_t s : b->st)
+        if (s) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->join)
+        if (e) cudaEventDestroy(e);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    if (b->own) cudaStreamDestroy(b->own);
+    delete b;
 }
 
 }  // extern "C"

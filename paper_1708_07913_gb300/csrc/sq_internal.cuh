@@ -156,6 +156,12 @@ int launch_weights(sq_ctx* ctx, const double* moments);
 int run_fermi(sq_ctx* ctx, const double* chi, const double* zeta, double Ne, double kT, double* mu);
 int run_density(sq_ctx* ctx, const double* chi, const double* zeta, double mu, double kT,
                 double* rho, double* eb, double* es, double* ne);
+// graph-capturable forms (no host wait): results stay in ctx->d_fermi
+int enqueue_fermi(sq_ctx* ctx, const double* chi, const double* zeta, double Ne, double kT);
+int enqueue_density(sq_ctx* ctx, const double* chi, const double* zeta, double mu, double kT, double* rho,
+                    int mu_from_state);
+constexpr int FERMI_STATE = 12;      // doubles of the device Fermi/energy state
+int fermi_result(const double* st_host, double* mu, double* eb, double* es, double* ne);
 int launch_proj_tables(sq_ctx* ctx, const double* d_R);
 }  // namespace sq
 

@@ -242,8 +242,14 @@ int launch_weights(sq_ctx* ctx, const double* moments)
     long long tot = ctx->g.Nd * K;
     size_t tbytes = (size_t)K * K * sizeof(double);
     int use_table = tbytes <= 96 * 1024;
-    if (use_table && tbytes > 48 * 1024)
-        cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbytes);
+    if (use_table && tbytes > 48 * 1024) {        // raise only (see the region kernels' dispatch)
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, weights_kernel) != cudaSuccess) return SQ_ECUDA;
+        if ((int)tbytes > fa.maxDynamicSharedSizeBytes &&
+            cudaFuncSetAttribute(weights_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tbytes) !=
+                cudaSuccess)
+            return SQ_ECUDA;
+    }
     int blocks = (int)std::min<long long>((tot + 255) / 256, (long long)ctx->sm_count * 8);
     weights_kernel<<<blocks, 256, use_table ? tbytes : 0, ctx->stream>>>(moments, ctx->d_W, ctx->g.Nd, K,
                                                                          use_table);
@@ -286,6 +292,7 @@ __device__ inline void block_reduce(double (&v)[NV], double* sh)
 
 // Fermi state layout (doubles)
 enum { F_LO = 0, F_HI, F_NE, F_KT, F_NLO, F_NHI, F_DONE, F_ITERS, F_STATUS, F_EB, F_ES, F_NEL, F_NSTATE };
+static_assert(F_NSTATE == FERMI_STATE, "Fermi state size");
 
 // min(chi - zeta) - 10 kT and max(chi + zeta) + 10 kT
 __global__ void fermi_bracket_kernel(const double* __restrict__ chi, const double* __restrict__ zeta, long long Nd,
@@ -393,14 +400,26 @@ __global__ void fermi_count_kernel(const double* __restrict__ W, const double* _
     }
 }
 
-int run_fermi(sq_ctx* ctx, const double* chi, const double* zeta, double Ne, double kT, double* mu)
+// Bisection state reset (a kernel rather than a host copy, so the whole
+// Fermi-level search can be captured in a CUDA graph).
+__global__ void fermi_init_kernel(double* st, double Ne, double kT)
+{
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < F_NSTATE; ++i) st[i] = 0.0;
+        st[F_NE] = Ne;
+        st[F_KT] = kT;
+    }
+}
+
+// Enqueue the whole Fermi-level search on ctx->stream (no host wait); the
+// result stays in the device state: mu = (st[F_LO] + st[F_HI]) / 2, status
+// in st[F_STATUS].
+int enqueue_fermi(sq_ctx* ctx, const double* chi, const double* zeta, double Ne, double kT)
 {
     const long long Nd = ctx->g.Nd;
     const int K = ctx->npl + 1;
-    double init[F_NSTATE] = {0};
-    init[F_NE] = Ne;
-    init[F_KT] = kT;
-    SQ_CUDA_TRY(cudaMemcpyAsync(ctx->d_fermi, init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    fermi_init_kernel<<<1, 32, 0, ctx->stream>>>(ctx->d_fermi, Ne, kT);
+    ctx->launches++;
     const int blocks = ctx->red_blocks;
     fermi_bracket_kernel<<<blocks, RED_T, 0, ctx->stream>>>(chi, zeta, Nd, ctx->d_red, ctx->d_count, ctx->d_fermi);
     fermi_count_kernel<<<blocks, RED_T, 0, ctx->stream>>>(ctx->d_W, chi, zeta, Nd, K, 0, ctx->d_red, ctx->d_count,
@@ -414,6 +433,13 @@ int run_fermi(sq_ctx* ctx, const double* chi, const double* zeta, double Ne, dou
         ctx->launches++;
     }
     SQ_CUDA_TRY(cudaGetLastError());
+    return SQ_OK;
+}
+
+int run_fermi(sq_ctx* ctx, const double* chi, const double* zeta, double Ne, double kT, double* mu)
+{
+    int rc = enqueue_fermi(ctx, chi, zeta, Ne, kT);
+    if (rc) return rc;
     double st[F_NSTATE];
     SQ_CUDA_TRY(cudaMemcpyAsync(st, ctx->d_fermi, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
     SQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));
@@ -422,16 +448,26 @@ int run_fermi(sq_ctx* ctx, const double* chi, const double* zeta, double Ne, dou
     return SQ_OK;
 }
 
+int fermi_result(const double* st_host, double* mu, double* eb, double* es, double* ne)
+{
+    if (mu) *mu = 0.5 * (st_host[F_LO] + st_host[F_HI]);
+    if (eb) *eb = st_host[F_EB];
+    if (es) *es = st_host[F_ES];
+    if (ne) *ne = st_host[F_NEL];
+    return st_host[F_STATUS] != 0.0 ? (int)st_host[F_STATUS] : SQ_OK;
+}
+
 // ------------------------------------------------------------------------
 // Density, band energy, entropy, electron count at mu.
 // ------------------------------------------------------------------------
 __global__ void density_kernel(const double* __restrict__ W, const double* __restrict__ chi,
                                const double* __restrict__ zeta, long long Nd, int K, double mu, double kT, double h,
-                               double* __restrict__ rho, double* red, unsigned* count, double* st)
+                               double* __restrict__ rho, double* red, unsigned* count, double* st, int mu_from_state)
 {
     __shared__ double sh[96];
     __shared__ bool last;
     __shared__ double xk[MAX_NPL + 1];
+    if (mu_from_state) mu = 0.5 * (((volatile double*)st)[F_LO] + ((volatile double*)st)[F_HI]);
     for (int k = threadIdx.x; k < K; k += blockDim.x) xk[k] = cos(M_PI * (k + 0.5) / K);
     __syncthreads();
     const double h3 = h * h * h;
@@ -490,14 +526,23 @@ __global__ void density_kernel(const double* __restrict__ W, const double* __res
     }
 }
 
-int run_density(sq_ctx* ctx, const double* chi, const double* zeta, double mu, double kT, double* rho,
-                double* eb, double* es, double* ne)
+int enqueue_density(sq_ctx* ctx, const double* chi, const double* zeta, double mu, double kT, double* rho,
+                    int mu_from_state)
 {
     const int blocks = ctx->red_blocks;
     density_kernel<<<blocks, RED_T, 0, ctx->stream>>>(ctx->d_W, chi, zeta, ctx->g.Nd, ctx->npl + 1, mu, kT,
-                                                     ctx->g.h, rho, ctx->d_red, ctx->d_count, ctx->d_fermi);
+                                                     ctx->g.h, rho, ctx->d_red, ctx->d_count, ctx->d_fermi,
+                                                     mu_from_state);
     ctx->launches++;
     SQ_CUDA_TRY(cudaGetLastError());
+    return SQ_OK;
+}
+
+int run_density(sq_ctx* ctx, const double* chi, const double* zeta, double mu, double kT, double* rho,
+                double* eb, double* es, double* ne)
+{
+    int rc = enqueue_density(ctx, chi, zeta, mu, kT, rho, 0);
+    if (rc) return rc;
     double st[F_NSTATE];
     SQ_CUDA_TRY(cudaMemcpyAsync(st, ctx->d_fermi, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
     SQ_CUDA_TRY(cudaStreamSynchronize(ctx->stream));

@@ -15,7 +15,16 @@ struct RegionDispatch {
         constexpr bool DB = fits_double_buffer<T, M>();
         size_t bytes = region_smem<T, M>() + extra;
         const void* fn = which == 0 ? (const void*)moments_kernel<T, M, DB> : (const void*)lanczos_kernel<T, M, DB>;
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
+        // the limit only ever grows: contexts that share this kernel (with
+        // different projector-table sizes) may launch in any order later,
+        // e.g. from one captured graph
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+            cudaGetLastError();
+            return SQ_ECUDA;
+        }
+        if ((int)bytes > fa.maxDynamicSharedSizeBytes &&
+            cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) != cudaSuccess) {
             cudaGetLastError();
             return SQ_EUNSUPPORTED;
         }

@@ -23,7 +23,8 @@ SQ_FP64, SQ_FP32 = 0, 1
 # Every entry point declared in include/sq.h.
 EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments", "sq_fermi_level",
            "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
-           "sq_strerror")
+           "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
+           "sq_batch_destroy")
 
 
 class SQError(RuntimeError):
@@ -66,6 +67,13 @@ def load(path: str = LIB_PATH):
         lib.sq_destroy.restype = None
         lib.sq_strerror.argtypes = [ip]
         lib.sq_strerror.restype = C.c_char_p
+        pp = C.POINTER(vp)
+        lib.sq_batch_create.argtypes = [C.POINTER(vp), ip, pp, vp]
+        lib.sq_batch_run.argtypes = [vp, pp, pp, pp, pp, pp, dp, dp, ip, C.c_double]
+        lib.sq_batch_results.argtypes = [vp, dp, dp, dp, dp]
+        lib.sq_batch_blocks.argtypes = [vp, C.POINTER(ip)]
+        lib.sq_batch_destroy.argtypes = [vp]
+        lib.sq_batch_destroy.restype = None
         if path == LIB_PATH:
             _lib = lib
         return lib
@@ -167,3 +175,48 @@ def sq_launch_count(ctx) -> int:
 def sq_destroy(ctx):
     if ctx:
         load().sq_destroy(C.c_void_p(ctx))
+
+
+def _ptrs(ts, name):
+    arr = (C.c_void_p * len(ts))(*[_dptr(t, f"{name}[{i}]") for i, t in enumerate(ts)])
+    return C.cast(arr, C.POINTER(C.c_void_p)), arr
+
+
+def _dbl(xs):
+    return (C.c_double * len(xs))(*[float(x) for x in xs])
+
+
+def sq_batch_create(ctxs, stream=None):
+    """Returns an opaque batch handle over the given context handles."""
+    lib = load()
+    b = C.c_void_p()
+    arr = (C.c_void_p * len(ctxs))(*[C.c_void_p(c) for c in ctxs])
+    _check(lib.sq_batch_create(C.byref(b), len(ctxs), C.cast(arr, C.POINTER(C.c_void_p)),
+                               stream if stream is not None else _stream()), "sq_batch_create")
+    return b.value
+
+
+def sq_batch_run(batch, V, chi, zeta, moments, rho, n_electrons, kT, n_lanczos, margin):
+    """Lists (one entry per system) of device tensors and per-system N_e, kT."""
+    keep = [_ptrs(V, "V"), _ptrs(chi, "chi"), _ptrs(zeta, "zeta"), _ptrs(moments, "moments"), _ptrs(rho, "rho")]
+    ne, kt = _dbl(n_electrons), _dbl(kT)
+    _check(load().sq_batch_run(C.c_void_p(batch), *[k[0] for k in keep], ne, kt, int(n_lanczos), float(margin)),
+           "sq_batch_run")
+
+
+def sq_batch_results(batch, n):
+    """Waits for the batch; returns lists (mu, E_band, E_ent, N)."""
+    out = [(C.c_double * n)() for _ in range(4)]
+    _check(load().sq_batch_results(C.c_void_p(batch), *out), "sq_batch_results")
+    return [list(o) for o in out]
+
+
+def sq_batch_blocks(batch, n):
+    out = (C.c_int * n)()
+    _check(load().sq_batch_blocks(C.c_void_p(batch), out), "sq_batch_blocks")
+    return list(out)
+
+
+def sq_batch_destroy(batch):
+    if batch:
+        load().sq_batch_destroy(C.c_void_p(batch))

@@ -159,3 +159,23 @@ def sample_nodes(n_nodes: int, count: int, seed: int = 7) -> np.ndarray:
     rng = np.random.default_rng(seed)
     count = min(count, n_nodes)
     return np.sort(rng.choice(n_nodes, size=count, replace=False)).astype(np.int64)
+
+
+def batch_workloads(count: int = 16, seed: int = 1724) -> list:
+    """Seeded uneven systems for the batched launch: 1^3..4^3 FCC cells,
+    nominal h in {0.45, 0.5} (n = round(a c / h)), R_cut in {4, 5, 6, 7} bohr,
+    n_pl in {24, 32, 48, 64}, kT uniform in [0.03, 0.2] Ha, displacements
+    sigma 0.15 bohr, s + 3p projectors.  The Lanczos bounds are widened by
+    2 % rather than 1 %: after the fixed 40 steps a few nodes of these
+    systems keep an extreme Ritz value up to ~1 % of the spectrum width
+    inside the spectrum (found by the enclosure check |rho^j| <= 1)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(count):
+        cells = int(rng.integers(1, 5))
+        h_nom = float(rng.choice([0.45, 0.5]))
+        n = int(round(LATTICE_A * cells / h_nom))
+        out.append(Workload(f"batch{count}_{i}", cells=cells, n=n, r_cut=float(rng.choice([4.0, 5.0, 6.0, 7.0])),
+                            npl=int(rng.choice([24, 32, 48, 64])), kT=float(rng.uniform(0.03, 0.2)),
+                            sigma_disp=0.15, nonlocal_=True, seed=seed + 1 + i, margin=0.02))
+    return out

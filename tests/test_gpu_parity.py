@@ -178,6 +178,40 @@ def test_edge_geometries_fp64_and_fp32(shape, r_cut, npl, nonlocal_):
         solver.close()
 
 
+@pytest.mark.parametrize("r_cut,count", [(6.0, 6), (7.0, 4)])
+def test_largest_regions_fp32_sampled(r_cut, count):
+    """The largest regions: h = 0.45 on one FCC cell (17^3 grid) with
+    R_cut = 6 (m = 13, 27^3 points) and R_cut = 7 (m = 15, 31^3, the largest
+    the library supports), s + 3p projectors.  Regions are wider than the
+    cell (infinite-cell method).  FP32 keeps the second vector in global
+    scratch here; the oracle recomputes bounds and moments of a node sample.
+    The FP64 form declines these sizes (they do not fit one CTA)."""
+    wl = synth.custom_workload("largest", cells=1, n=17, r_cut=r_cut, npl=32, kT=0.1, sigma_disp=0.15,
+                               nonlocal_=True, seed=1721)
+    s = synth.make_system(wl)
+    assert wl.m == {6.0: 13, 7.0: 15}[r_cut]
+    nodes = synth.sample_nodes(wl.n_nodes, count, seed=3)
+    osys = oracle.OracleSystem.from_synth(s)
+    ochi, ozeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
+    omom = osys.moments(nodes, ochi, ozeta, wl.npl)
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP32, device=DEV)
+    V = _dev(s.V)
+    chi, zeta = solver.bounds(V, wl.n_lanczos, wl.margin)
+    np.testing.assert_allclose(chi.cpu().numpy()[nodes], ochi, rtol=2e-4)
+    np.testing.assert_allclose(zeta.cpu().numpy()[nodes], ozeta, rtol=2e-4)
+    chi2, zeta2 = chi.clone(), zeta.clone()
+    idx = torch.from_numpy(nodes).to(DEV)
+    chi2[idx] = _dev(ochi)
+    zeta2[idx] = _dev(ozeta)
+    mom = solver.compute_moments(V, chi2, zeta2).cpu().numpy()
+    np.testing.assert_allclose(mom[nodes], omom, rtol=0, atol=FP32_MOM)
+    assert np.all(np.abs(mom) <= 1 + 1e-4)
+    solver.close()
+    with pytest.raises(SQError) as e:
+        SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    assert e.value.code == sq.SQ_EUNSUPPORTED
+
+
 def test_errors_are_reported_not_faulted():
     s = synth.make_system("al4_16")
     wl = s.wl
