@@ -5,9 +5,11 @@ benchmark's CPU-baseline leg are the only callers.  The CUDA library never
 imports, links or calls anything here, and this package imports nothing from
 the CUDA package; the two share only the seeded input generator ``synth``.
 
-``sq_oracle.c`` holds the arithmetic (each function cites the passage of the
-paper it follows); this module only compiles it with gcc and marshals numpy
-arrays through ctypes.
+``sq_oracle.c`` (the SQ path) and ``scf_oracle.c`` (Poisson, exchange and
+mixing of the SCF loop around it) hold the arithmetic (each function cites
+the passage of the paper it follows); this module only compiles them with
+gcc, marshals numpy arrays through ctypes, and strings the SCF loop together
+from those calls.
 """
 from __future__ import annotations
 
@@ -20,6 +22,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "sq_oracle.c")
+_SRC_SCF = os.path.join(_HERE, "scf_oracle.c")
 _LIB = os.path.join(_HERE, "libsq_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -27,10 +30,11 @@ _lib = None
 
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (no FMA contraction, so x86 and Arm agree)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC_SCF))
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < newest:
         tmp = _LIB + f".tmp{os.getpid()}"
         subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
-                               "-std=gnu11", "-o", tmp, _SRC, "-lm"])
+                               "-std=gnu11", "-o", tmp, _SRC, _SRC_SCF, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -67,6 +71,12 @@ def _load():
             lib.or_fermi_level.argtypes = [C.c_long, C.c_int, dp, dp, dp, C.c_double, C.c_double, dp, ip]
             lib.or_density_energy.argtypes = [C.c_long, C.c_int, dp, dp, dp, C.c_double, C.c_double,
                                               C.c_double, dp, dp, dp, dp]
+            lib.or_laplacian_periodic.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp]
+            lib.or_poisson_cg.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp, C.c_double,
+                                          C.c_int, ip, dp]
+            lib.or_xalpha.argtypes = [C.c_long, dp, C.c_double, dp]
+            lib.or_xalpha.restype = None
+            lib.or_anderson_step.argtypes = [C.c_long, C.c_int, dp, dp, C.c_double, dp]
             _lib = lib
     return _lib
 
@@ -226,3 +236,79 @@ def solve(osys: OracleSystem, npl, kT, n_electrons, n_lanczos=40, margin=0.01, n
     rho, eb, es, ne = density_energy(W, chi, zeta, mu, kT, osys.h)
     return dict(chi=chi, zeta=zeta, moments=mom, W=W, mu=mu, bisection_steps=it, rho=rho,
                 e_band=eb, e_ent=es, n_elec=ne)
+
+
+# ---------------------------------------------------------------------------
+# SCF loop pieces (scf_oracle.c) and the loop itself
+# ---------------------------------------------------------------------------
+def laplacian_periodic(x, h, no=6):
+    """-lap_h x on the periodic grid; x has shape (n3, n2, n1)."""
+    x = _f64(x)
+    y = np.zeros_like(x)
+    n3, n2, n1 = x.shape
+    if _load().or_laplacian_periodic(n1, n2, n3, float(h), int(no), _dp(x), _dp(y)) != 0:
+        raise ValueError("bad FD parameters")
+    return y
+
+
+def poisson(rho, h, no=6, tol=1e-12, max_iter=5000):
+    """phi with -(1/4 pi) lap_h phi = rho - mean(rho), zero mean (periodic);
+    returns (phi, iterations, relative residual)."""
+    rho = _f64(rho)
+    phi = np.zeros_like(rho)
+    n3, n2, n1 = rho.shape
+    it, res = C.c_int(), C.c_double()
+    rc = _load().or_poisson_cg(n1, n2, n3, float(h), int(no), _dp(rho), _dp(phi), float(tol), int(max_iter),
+                               C.byref(it), C.byref(res))
+    if rc == 1:
+        raise ValueError("bad arguments")
+    return phi, it.value, res.value
+
+
+def xalpha(rho, alpha=2.0 / 3.0):
+    rho = _f64(rho)
+    vx = np.zeros_like(rho)
+    _load().or_xalpha(rho.size, _dp(rho), float(alpha), _dp(vx))
+    return vx
+
+
+def anderson_step(Xs, Fs, beta):
+    """Xs, Fs: (mh + 1, n) iterates and residuals, oldest first."""
+    Xs, Fs = _f64(Xs), _f64(Fs)
+    out = np.zeros(Xs.shape[1])
+    rc = _load().or_anderson_step(Xs.shape[1], Xs.shape[0] - 1, _dp(Xs), _dp(Fs), float(beta), _dp(out))
+    if rc > 1:
+        raise ValueError("bad history")
+    return out
+
+
+def scf(V_loc, h, m, positions, proj_types, n_electrons, kT, npl, alpha=2.0 / 3.0, beta=0.3, history=7,
+        tol=1e-6, max_iter=60, n_lanczos=40, margin=0.01, periodic=False, fd_half_order=6, poisson_tol=1e-12):
+    """The SCF loop of Section 3 around the SQ path, with the effective
+    potential as the fixed-point variable: V_in -> SQ density rho[V_in] ->
+    V_out = V_loc + phi[rho] + v_x[rho] (phi: Eq. PoissonEqn with a
+    neutralising background; v_x: Slater X-alpha), stopped when
+    ||V_out - V_in|| <= tol ||V_out|| (2-norms); Anderson mixing with the last
+    `history` differences.  Starts from V_in = V_loc.  Returns a dict with the
+    converged V_in, rho, mu, energies, the residual history and iterations."""
+    V_loc = _f64(V_loc)
+    V_in = V_loc.copy()
+    Xs, Fs, res = [], [], []
+    out = None
+    for it in range(max_iter):
+        osys = OracleSystem(V_in, h, m, positions, proj_types, fd_half_order, periodic)
+        out = solve(osys, npl, kT, n_electrons, n_lanczos, margin)
+        rho = out["rho"].reshape(V_loc.shape)
+        phi, _, _ = poisson(rho, h, fd_half_order, poisson_tol)
+        V_out = V_loc + phi + xalpha(rho, alpha)
+        f = (V_out - V_in).ravel()
+        res.append(float(np.linalg.norm(f) / np.linalg.norm(V_out)))
+        if res[-1] <= tol:
+            return dict(V=V_in, V_out=V_out, rho=rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
+                        n_elec=out["n_elec"], residuals=res, iterations=it + 1, converged=True)
+        Xs.append(V_in.ravel().copy())
+        Fs.append(f.copy())
+        Xs, Fs = Xs[-(history + 1):], Fs[-(history + 1):]
+        V_in = anderson_step(np.array(Xs), np.array(Fs), beta).reshape(V_loc.shape)
+    return dict(V=V_in, rho=out["rho"].reshape(V_loc.shape), mu=out["mu"], residuals=res, iterations=max_iter,
+                converged=False)
