@@ -220,6 +220,52 @@ int sq_batch_results(sq_batch *b, double *mu_host, double *e_band_host, double *
 int sq_batch_blocks(const sq_batch *b, int *blocks_host);
 void sq_batch_destroy(sq_batch *b);
 
+/* ---------------------------------------------------------------------------
+ * Self-consistent field (SCF) loop around the path.  The paper iterates on
+ * the effective potential V_eff = V_xc + phi (Section 3, footnote on the SCF
+ * method), with phi from the Poisson problem of Eq. PoissonEqn solved by AAR
+ * and Periodic Pulay mixing; these calls provide the conjugate-gradient,
+ * Slater X-alpha and Anderson-mixing counterparts, on the device.
+ *
+ * sq_poisson(ctx, rho, phi, tol, max_iter, iters_host, rel_resid_host)
+ *   phi solves -(1/4 pi) lap_h phi = rho - mean(rho) on the context's
+ *   periodic grid (Eq. PoissonEqn with the pseudocharges replaced by the
+ *   uniform neutralising background; lap_h the Laplacian of
+ *   Eq. FD:Laplacian with the context's order), phi with zero mean.
+ *   Conjugate gradients from phi = 0 until ||b - A phi|| <= tol ||b||,
+ *   b = 4 pi (rho - mean(rho)); a neutral rho (b below 1e-13 of 4 pi ||rho||)
+ *   gives phi = 0.  rho, phi: device, N_d FP64.  0 < tol < 1, max_iter >= 0.
+ *   iters_host, rel_resid_host: HOST outputs (may be NULL).  SQ_ENOCONV if
+ *   max_iter is reached first.  Allocates 4 N_d doubles of workspace in the
+ *   context on first use.  Synchronises the stream.
+ * sq_effective_potential(ctx, V_loc, phi, rho, alpha, V_out)
+ *   V_out = V_loc + phi + v_x(rho), v_x = -(3 alpha / 2)(3 rho / pi)^(1/3)
+ *   (Slater X-alpha; alpha = 2/3 is uniform-gas exchange; 0 where rho <= 0).
+ *   All device, N_d FP64; 0 < alpha < 10.  Asynchronous.
+ * sq_mixer_create(out, n, history, beta, cuda_stream)
+ *   An Anderson mixer for vectors of n doubles keeping the last `history`
+ *   (0..16) differences, mixing parameter 0 < beta <= 1, on cuda_stream
+ *   (NULL = legacy).  Allocates 2 (history + 1) n doubles.
+ * sq_mixer_step(mx, v_in, v_out, v_next, rel_resid_host)
+ *   For the fixed-point map v_in -> v_out (residual f = v_out - v_in):
+ *   records (v_in, f), returns ||f|| / ||v_out|| in rel_resid_host (HOST,
+ *   may be NULL) and writes v_next = v_in + beta f - (dX + beta dF) gamma,
+ *   gamma minimising ||f - dF gamma|| over the stored differences (if their
+ *   normal equations are numerically singular the history is not used).
+ *   Device vectors of n doubles.  Synchronises the mixer's stream.
+ * sq_mixer_reset(mx): forget the history.  sq_mixer_destroy(mx): release.
+ * ------------------------------------------------------------------------- */
+int sq_poisson(sq_ctx *ctx, const double *rho, double *phi, double tol, int max_iter,
+               int *iters_host, double *rel_resid_host);
+int sq_effective_potential(sq_ctx *ctx, const double *V_loc, const double *phi, const double *rho,
+                           double alpha, double *V_out);
+typedef struct sq_mixer sq_mixer;
+int sq_mixer_create(sq_mixer **out, long long n, int history, double beta, void *cuda_stream);
+int sq_mixer_step(sq_mixer *mx, const double *v_in, const double *v_out, double *v_next,
+                  double *rel_resid_host);
+int sq_mixer_reset(sq_mixer *mx);
+void sq_mixer_destroy(sq_mixer *mx);
+
 /* Wait for the context's stream and return any latched device error. */
 int sq_sync(sq_ctx *ctx);
 

@@ -13,7 +13,7 @@ from __future__ import annotations
 from . import sq
 from .sq import SQ_FP32, SQ_FP64, SQError
 
-__all__ = ["sq", "SQSolver", "SQBatch", "SQ_FP32", "SQ_FP64", "SQError", "build"]
+__all__ = ["sq", "SQSolver", "SQBatch", "SQSCF", "SQ_FP32", "SQ_FP64", "SQError", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -128,6 +128,63 @@ class SQBatch:
         if getattr(self, "batch", None):
             sq.sq_batch_destroy(self.batch)
             self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SQSCF:
+    """The SCF loop around the path for one SQSolver: the effective potential
+    is the fixed-point variable (V_in -> SQ density -> V_out = V_loc + phi +
+    v_x, Anderson-mixed), stopped when ||V_out - V_in|| <= tol ||V_out||.
+    Every step runs in libsq (sq_* calls, include/sq.h); this class only
+    sequences them."""
+
+    def __init__(self, solver, V_loc, n_electrons, kT, alpha=2.0 / 3.0, beta=0.3, history=7, n_lanczos=40,
+                 margin=0.01):
+        torch = solver.torch
+        self.solver, self.V_loc = solver, V_loc
+        self.n_electrons, self.kT, self.alpha = float(n_electrons), float(kT), float(alpha)
+        self.n_lanczos, self.margin = int(n_lanczos), float(margin)
+        f64 = dict(dtype=torch.float64, device=solver.device)
+        self.phi = torch.empty(solver.n_nodes, **f64)
+        self.V_out = torch.empty(solver.n_nodes, **f64)
+        self._V = [torch.empty(solver.n_nodes, **f64), torch.empty(solver.n_nodes, **f64)]
+        with torch.cuda.device(solver.device):
+            self.mixer = sq.sq_mixer_create(solver.n_nodes, history, beta)
+
+    def run(self, V0=None, tol=1e-6, max_iter=60, poisson_tol=1e-12):
+        """Returns a dict: V (the converged input potential), rho, mu,
+        e_band, e_ent, n_elec, residuals, iterations, converged, poisson
+        iterations per SCF step."""
+        sv = self.solver
+        sq.sq_mixer_reset(self.mixer)
+        V_in, V_next = self._V
+        V_in.copy_(self.V_loc if V0 is None else V0)
+        res, pit, out = [], [], None
+        for it in range(max_iter):
+            out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
+            sq.sq_set_stream(sv.ctx)
+            k, _ = sq.sq_poisson(sv.ctx, sv.rho, self.phi, poisson_tol)
+            pit.append(k)
+            sq.sq_effective_potential(sv.ctx, self.V_loc, self.phi, sv.rho, self.alpha, self.V_out)
+            res.append(sq.sq_mixer_step(self.mixer, V_in, self.V_out, V_next))
+            if res[-1] <= tol:
+                return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
+                            n_elec=out["n_elec"], residuals=res, iterations=it + 1, converged=True,
+                            poisson_iterations=pit)
+            V_in, V_next = V_next, V_in
+        return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
+                    n_elec=out["n_elec"], residuals=res, iterations=max_iter, converged=False,
+                    poisson_iterations=pit)
+
+    def close(self):
+        if getattr(self, "mixer", None):
+            sq.sq_mixer_destroy(self.mixer)
+            self.mixer = None
 
     def __del__(self):
         try:

@@ -72,6 +72,7 @@ void free_ctx(sq_ctx* c)
                     c->d_alpha, c->d_beta, c->d_klen, c->d_W, c->d_red, c->d_fermi, c->d_count, c->d_err};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    free_poisson_ws(c);
     delete c;
 }
 

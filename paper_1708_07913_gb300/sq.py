@@ -24,7 +24,8 @@ SQ_FP64, SQ_FP32 = 0, 1
 EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments", "sq_fermi_level",
            "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
-           "sq_batch_destroy")
+           "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
+           "sq_mixer_reset", "sq_mixer_destroy")
 
 
 class SQError(RuntimeError):
@@ -74,6 +75,13 @@ def load(path: str = LIB_PATH):
         lib.sq_batch_blocks.argtypes = [vp, C.POINTER(ip)]
         lib.sq_batch_destroy.argtypes = [vp]
         lib.sq_batch_destroy.restype = None
+        lib.sq_poisson.argtypes = [vp, vp, vp, C.c_double, ip, C.POINTER(ip), dp]
+        lib.sq_effective_potential.argtypes = [vp, vp, vp, vp, C.c_double, vp]
+        lib.sq_mixer_create.argtypes = [C.POINTER(vp), C.c_longlong, ip, C.c_double, vp]
+        lib.sq_mixer_step.argtypes = [vp, vp, vp, vp, dp]
+        lib.sq_mixer_reset.argtypes = [vp]
+        lib.sq_mixer_destroy.argtypes = [vp]
+        lib.sq_mixer_destroy.restype = None
         if path == LIB_PATH:
             _lib = lib
         return lib
@@ -220,3 +228,40 @@ def sq_batch_blocks(batch, n):
 def sq_batch_destroy(batch):
     if batch:
         load().sq_batch_destroy(C.c_void_p(batch))
+
+
+def sq_poisson(ctx, rho, phi, tol=1e-12, max_iter=5000):
+    """Fills phi; returns (iterations, relative residual)."""
+    it, res = C.c_int(), C.c_double()
+    _check(load().sq_poisson(C.c_void_p(ctx), _dptr(rho, "rho"), _dptr(phi, "phi"), float(tol), int(max_iter),
+                             C.byref(it), C.byref(res)), "sq_poisson")
+    return it.value, res.value
+
+
+def sq_effective_potential(ctx, V_loc, phi, rho, alpha, V_out):
+    _check(load().sq_effective_potential(C.c_void_p(ctx), _dptr(V_loc, "V_loc"), _dptr(phi, "phi"),
+                                         _dptr(rho, "rho"), float(alpha), _dptr(V_out, "V_out")),
+           "sq_effective_potential")
+
+
+def sq_mixer_create(n, history, beta, stream=None):
+    m = C.c_void_p()
+    _check(load().sq_mixer_create(C.byref(m), int(n), int(history), float(beta),
+                                  stream if stream is not None else _stream()), "sq_mixer_create")
+    return m.value
+
+
+def sq_mixer_step(mixer, v_in, v_out, v_next) -> float:
+    res = C.c_double()
+    _check(load().sq_mixer_step(C.c_void_p(mixer), _dptr(v_in, "v_in"), _dptr(v_out, "v_out"),
+                                _dptr(v_next, "v_next"), C.byref(res)), "sq_mixer_step")
+    return res.value
+
+
+def sq_mixer_reset(mixer):
+    _check(load().sq_mixer_reset(C.c_void_p(mixer)), "sq_mixer_reset")
+
+
+def sq_mixer_destroy(mixer):
+    if mixer:
+        load().sq_mixer_destroy(C.c_void_p(mixer))

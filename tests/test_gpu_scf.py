@@ -1,0 +1,107 @@
+"""The SCF loop's device pieces (sq_poisson, sq_effective_potential,
+sq_mixer_*) against the oracle (oracle/scf_oracle.c, pinned by
+tests/test_oracle_scf.py), and the whole loop (SQSCF) against oracle.scf on
+a small infinite-cell system."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1708_07913_gb300 import SQ_FP64, SQSCF, SQSolver, build, sq  # noqa: E402
+
+build()
+DEV = "cuda:0"
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(DEV)
+
+
+@pytest.fixture(scope="module")
+def small():
+    s = synth.make_system("al4_16")
+    solver = SQSolver.from_workload(s.wl, s.positions, precision=SQ_FP64, device=DEV)
+    yield s, solver
+    solver.close()
+
+
+def test_poisson_matches_oracle(small):
+    s, solver = small
+    n = s.wl.n
+    rng = np.random.default_rng(7)
+    rho = rng.uniform(0.0, 0.05, size=(n, n, n)) + 0.02 * np.exp(-((np.arange(n) - n / 2) ** 2) / 8)[None, None, :]
+    phi_ref, _, _ = oracle.poisson(rho, s.wl.h, tol=1e-13)
+    phi = torch.empty(n ** 3, dtype=torch.float64, device=DEV)
+    sq.sq_set_stream(solver.ctx)
+    it, res = sq.sq_poisson(solver.ctx, _dev(rho), phi, 1e-13)
+    assert res <= 1e-13 and it > 0
+    np.testing.assert_allclose(phi.cpu().numpy(), phi_ref.ravel(), atol=1e-10 * np.abs(phi_ref).max())
+    assert abs(phi.cpu().numpy().mean()) < 1e-13 * np.abs(phi_ref).max()
+    it0, _ = sq.sq_poisson(solver.ctx, _dev(np.full(n ** 3, 0.013)), phi, 1e-12)   # neutral density
+    assert it0 == 0 and np.all(phi.cpu().numpy() == 0.0)
+    with pytest.raises(sq.SQError) as e:                                            # too few iterations
+        sq.sq_poisson(solver.ctx, _dev(rho), phi, 1e-13, max_iter=3)
+    assert e.value.code == sq.SQ_ENOCONV
+
+
+def test_effective_potential_matches_oracle(small):
+    s, solver = small
+    N = s.wl.n_nodes
+    rng = np.random.default_rng(8)
+    rho = rng.uniform(-1e-3, 0.2, size=N)
+    phi = rng.standard_normal(N)
+    V_out = torch.empty(N, dtype=torch.float64, device=DEV)
+    for alpha in (2.0 / 3.0, 0.7):
+        sq.sq_effective_potential(solver.ctx, _dev(s.V), _dev(phi), _dev(rho), alpha, V_out)
+        ref = s.V.ravel() + phi + oracle.xalpha(rho, alpha)
+        np.testing.assert_allclose(V_out.cpu().numpy(), ref, rtol=1e-14, atol=1e-14)
+
+
+def test_mixer_matches_oracle():
+    rng = np.random.default_rng(9)
+    n, hist, beta = 777, 4, 0.35
+    mixer = sq.sq_mixer_create(n, hist, beta)
+    Xs, Fs = [], []
+    v_next = torch.empty(n, dtype=torch.float64, device=DEV)
+    x = rng.standard_normal(n)
+    for k in range(9):
+        v_out = 0.6 * np.tanh(x) + rng.standard_normal(n) * 0.1 + 1.0
+        res = sq.sq_mixer_step(mixer, _dev(x), _dev(v_out), v_next)
+        f = v_out - x
+        assert abs(res - np.linalg.norm(f) / np.linalg.norm(v_out)) < 1e-13 * res
+        Xs.append(x.copy())
+        Fs.append(f)
+        Xs, Fs = Xs[-(hist + 1):], Fs[-(hist + 1):]
+        ref = oracle.anderson_step(np.array(Xs), np.array(Fs), beta)
+        np.testing.assert_allclose(v_next.cpu().numpy(), ref, rtol=0, atol=1e-11 * np.abs(ref).max())
+        x = v_next.cpu().numpy().copy()
+    sq.sq_mixer_destroy(mixer)
+
+
+def test_scf_matches_oracle_scf():
+    """One FCC cell, 8^3 grid (h = 0.956), R_cut = 2.5 (5^3 regions), s + 3p
+    projectors, kT = 0.1: the device SCF follows the oracle's SCF (same
+    iteration count) and reaches the same fixed point."""
+    wl = synth.custom_workload("scf8", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1741)
+    s = synth.make_system(wl)
+    pt = synth.projector_types(True)
+    ref = oracle.scf(s.V, wl.h, wl.m, s.positions, pt, wl.n_electrons, wl.kT, wl.npl, tol=1e-9, max_iter=60)
+    assert ref["converged"]
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    scf = SQSCF(solver, _dev(s.V), wl.n_electrons, wl.kT)
+    out = scf.run(tol=1e-9, max_iter=60)
+    assert out["converged"] and abs(out["iterations"] - ref["iterations"]) <= 1
+    np.testing.assert_allclose(out["residuals"][:5], ref["residuals"][:5], rtol=1e-6)
+    np.testing.assert_allclose(out["V"].cpu().numpy(), ref["V"].ravel(), atol=1e-7 * np.abs(ref["V"]).max())
+    np.testing.assert_allclose(out["rho"].cpu().numpy(), ref["rho"].ravel(), atol=1e-7 * ref["rho"].max())
+    assert abs(out["mu"] - ref["mu"]) < 1e-7
+    assert abs(out["n_elec"] - wl.n_electrons) < 1e-8 * wl.n_electrons
+    scf.close()
+    solver.close()
