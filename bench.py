@@ -26,6 +26,7 @@ import math
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -109,8 +110,8 @@ class ClockSampler:
 
     def start(self):
         try:
-            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{self.gpu}.csv")
+            # raw samples go to the temp directory; the JSON line carries their summary
+            self.path = os.path.join(tempfile.gettempdir(), f"sq_bench_clocks_gpu{self.gpu}_{os.getpid()}.csv")
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + ",".join(SMI_FIELDS),
                                           "--format=csv,noheader,nounits", "-lms", "200"],
