@@ -253,6 +253,11 @@ void sq_batch_destroy(sq_batch *b);
  *   gamma minimising ||f - dF gamma|| over the stored differences (if their
  *   normal equations are numerically singular the history is not used).
  *   Device vectors of n doubles.  Synchronises the mixer's stream.
+ * sq_mixer_history(mx, count_host): pairs currently stored (0..history+1).
+ * sq_mixer_export(mx, X_host, F_host): copy the stored iterates and residuals,
+ *   oldest first, into HOST arrays of count x n doubles each (for a
+ *   checkpoint).  sq_mixer_import(mx, count, X_host, F_host): replace the
+ *   history by count <= history + 1 such pairs (resuming from a checkpoint).
  * sq_mixer_reset(mx): forget the history.  sq_mixer_destroy(mx): release.
  * ------------------------------------------------------------------------- */
 int sq_poisson(sq_ctx *ctx, const double *rho, double *phi, double tol, int max_iter,
@@ -263,6 +268,9 @@ typedef struct sq_mixer sq_mixer;
 int sq_mixer_create(sq_mixer **out, long long n, int history, double beta, void *cuda_stream);
 int sq_mixer_step(sq_mixer *mx, const double *v_in, const double *v_out, double *v_next,
                   double *rel_resid_host);
+int sq_mixer_history(const sq_mixer *mx, int *count_host);
+int sq_mixer_export(sq_mixer *mx, double *X_host, double *F_host);
+int sq_mixer_import(sq_mixer *mx, int count, const double *X_host, const double *F_host);
 int sq_mixer_reset(sq_mixer *mx);
 void sq_mixer_destroy(sq_mixer *mx);
 

@@ -156,16 +156,26 @@ class SQSCF:
         with torch.cuda.device(solver.device):
             self.mixer = sq.sq_mixer_create(solver.n_nodes, history, beta)
 
-    def run(self, V0=None, tol=1e-6, max_iter=60, poisson_tol=1e-12):
+    def run(self, V0=None, tol=1e-6, max_iter=60, poisson_tol=1e-12, checkpoint=None, resume=None):
         """Returns a dict: V (the converged input potential), rho, mu,
         e_band, e_ent, n_elec, residuals, iterations, converged, poisson
-        iterations per SCF step."""
+        iterations per SCF step.  ``checkpoint``: a path; after every
+        iteration the next input potential and the mixing history are saved
+        there (.npz of .npy arrays).  ``resume``: such a file; the loop
+        continues from it (V0 is then ignored)."""
+        import numpy as np
         sv = self.solver
         sq.sq_mixer_reset(self.mixer)
         V_in, V_next = self._V
-        V_in.copy_(self.V_loc if V0 is None else V0)
         res, pit, out = [], [], None
-        for it in range(max_iter):
+        if resume is not None:
+            ck = np.load(resume)
+            V_in.copy_(self.solver.torch.from_numpy(ck["V"]))
+            sq.sq_mixer_import(self.mixer, ck["X"], ck["F"])
+            res = list(ck["residuals"])
+        else:
+            V_in.copy_(self.V_loc if V0 is None else V0)
+        for it in range(len(res), max_iter):
             out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
             sq.sq_set_stream(sv.ctx)
             k, _ = sq.sq_poisson(sv.ctx, sv.rho, self.phi, poisson_tol)
@@ -177,6 +187,9 @@ class SQSCF:
                             n_elec=out["n_elec"], residuals=res, iterations=it + 1, converged=True,
                             poisson_iterations=pit)
             V_in, V_next = V_next, V_in
+            if checkpoint is not None:
+                X, F = sq.sq_mixer_export(self.mixer, sv.n_nodes)
+                np.savez(checkpoint, V=V_in.cpu().numpy(), X=X, F=F, residuals=np.array(res))
         return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
                     n_elec=out["n_elec"], residuals=res, iterations=max_iter, converged=False,
                     poisson_iterations=pit)

@@ -477,6 +477,45 @@ int sq_mixer_step(sq_mixer* m, const double* v_in, const double* v_out, double* 
     return SQ_OK;
 }
 
+int sq_mixer_history(const sq_mixer* m, int* count_host)
+{
+    if (!m || !count_host) return SQ_EINVAL;
+    *count_host = (int)m->order.size();
+    return SQ_OK;
+}
+
+int sq_mixer_export(sq_mixer* m, double* X_host, double* F_host)
+{
+    if (!m || (!m->order.empty() && (!X_host || !F_host))) return SQ_EINVAL;
+    const size_t bytes = sizeof(double) * (size_t)m->n;
+    for (size_t i = 0; i < m->order.size(); ++i)
+        if (cudaMemcpyAsync(X_host + i * m->n, m->X[m->order[i]], bytes, cudaMemcpyDeviceToHost, m->st) != cudaSuccess ||
+            cudaMemcpyAsync(F_host + i * m->n, m->F[m->order[i]], bytes, cudaMemcpyDeviceToHost, m->st) != cudaSuccess) {
+            cudaGetLastError();
+            return SQ_ECUDA;
+        }
+    if (cudaStreamSynchronize(m->st) != cudaSuccess) return SQ_ECUDA;
+    return SQ_OK;
+}
+
+int sq_mixer_import(sq_mixer* m, int count, const double* X_host, const double* F_host)
+{
+    if (!m || count < 0 || count > m->hist + 1 || (count > 0 && (!X_host || !F_host))) return SQ_EINVAL;
+    const size_t bytes = sizeof(double) * (size_t)m->n;
+    m->order.clear();
+    for (int i = 0; i < count; ++i) {
+        if (cudaMemcpyAsync(m->X[i], X_host + (size_t)i * m->n, bytes, cudaMemcpyHostToDevice, m->st) != cudaSuccess ||
+            cudaMemcpyAsync(m->F[i], F_host + (size_t)i * m->n, bytes, cudaMemcpyHostToDevice, m->st) != cudaSuccess) {
+            cudaGetLastError();
+            m->order.clear();
+            return SQ_ECUDA;
+        }
+        m->order.push_back(i);
+    }
+    if (cudaStreamSynchronize(m->st) != cudaSuccess) return SQ_ECUDA;
+    return SQ_OK;
+}
+
 int sq_mixer_reset(sq_mixer* m)
 {
     if (!m) return SQ_EINVAL;

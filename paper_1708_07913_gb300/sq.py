@@ -25,7 +25,7 @@ EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments",
            "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
            "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
-           "sq_mixer_reset", "sq_mixer_destroy")
+           "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy")
 
 
 class SQError(RuntimeError):
@@ -79,6 +79,9 @@ def load(path: str = LIB_PATH):
         lib.sq_effective_potential.argtypes = [vp, vp, vp, vp, C.c_double, vp]
         lib.sq_mixer_create.argtypes = [C.POINTER(vp), C.c_longlong, ip, C.c_double, vp]
         lib.sq_mixer_step.argtypes = [vp, vp, vp, vp, dp]
+        lib.sq_mixer_history.argtypes = [vp, C.POINTER(ip)]
+        lib.sq_mixer_export.argtypes = [vp, dp, dp]
+        lib.sq_mixer_import.argtypes = [vp, ip, dp, dp]
         lib.sq_mixer_reset.argtypes = [vp]
         lib.sq_mixer_destroy.argtypes = [vp]
         lib.sq_mixer_destroy.restype = None
@@ -256,6 +259,25 @@ def sq_mixer_step(mixer, v_in, v_out, v_next) -> float:
     _check(load().sq_mixer_step(C.c_void_p(mixer), _dptr(v_in, "v_in"), _dptr(v_out, "v_out"),
                                 _dptr(v_next, "v_next"), C.byref(res)), "sq_mixer_step")
     return res.value
+
+
+def sq_mixer_export(mixer, n):
+    """The stored history as numpy arrays (X, F), each (count, n), oldest first."""
+    lib = load()
+    cnt = C.c_int()
+    _check(lib.sq_mixer_history(C.c_void_p(mixer), C.byref(cnt)), "sq_mixer_history")
+    X = np.zeros((cnt.value, n))
+    F = np.zeros((cnt.value, n))
+    _check(lib.sq_mixer_export(C.c_void_p(mixer), X.ctypes.data_as(C.POINTER(C.c_double)),
+                               F.ctypes.data_as(C.POINTER(C.c_double))), "sq_mixer_export")
+    return X, F
+
+
+def sq_mixer_import(mixer, X, F):
+    X = np.ascontiguousarray(X, dtype=np.float64)
+    F = np.ascontiguousarray(F, dtype=np.float64)
+    _check(load().sq_mixer_import(C.c_void_p(mixer), int(X.shape[0]), X.ctypes.data_as(C.POINTER(C.c_double)),
+                                  F.ctypes.data_as(C.POINTER(C.c_double))), "sq_mixer_import")
 
 
 def sq_mixer_reset(mixer):

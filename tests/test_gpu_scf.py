@@ -105,3 +105,25 @@ def test_scf_matches_oracle_scf():
     assert abs(out["n_elec"] - wl.n_electrons) < 1e-8 * wl.n_electrons
     scf.close()
     solver.close()
+
+
+def test_scf_checkpoint_and_resume(tmp_path):
+    """An SCF stopped after 4 iterations and resumed from its checkpoint (the
+    next input potential and the mixing history) takes the same iterations
+    as one that ran through, and reaches the same fixed point."""
+    wl = synth.custom_workload("scf8r", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1742)
+    s = synth.make_system(wl)
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    scf = SQSCF(solver, _dev(s.V), wl.n_electrons, wl.kT)
+    full = scf.run(tol=1e-9, max_iter=60)
+    V_full = full["V"].cpu().numpy().copy()
+    ck = str(tmp_path / "scf.npz")
+    part = scf.run(tol=1e-9, max_iter=4, checkpoint=ck)
+    assert not part["converged"] and len(part["residuals"]) == 4
+    rest = scf.run(tol=1e-9, max_iter=60, resume=ck)
+    assert rest["converged"] and rest["iterations"] == full["iterations"]
+    np.testing.assert_allclose(rest["residuals"], full["residuals"], rtol=1e-9)
+    np.testing.assert_allclose(rest["V"].cpu().numpy(), V_full, atol=1e-12 * np.abs(V_full).max())
+    scf.close()
+    solver.close()
