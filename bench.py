@@ -86,10 +86,16 @@ def flops_lanczos(wl):
     return wl.n_nodes * wl.n_lanczos * S ** 3 * per_point
 
 
+# the sources that define the region kernels (their counters are recorded
+# against this hash, so any change to these files voids them)
+KERNEL_SOURCES = ("sq_internal.cuh", "sq_region.cuh", "sq_region_dispatch.cuh", "sq_region_f32.cu",
+                  "sq_region_f64.cu")
+
+
 def source_sha():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1708_07913_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in KERNEL_SOURCES:
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 

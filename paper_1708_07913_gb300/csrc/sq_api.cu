@@ -21,6 +21,10 @@ int region_launch_f64(int m, int which, const RegionArgs<double>& a, size_t extr
 
 using namespace sq;
 
+namespace sq {
+void free_poisson_ws(sq_ctx* ctx);   // sq_scf.cu: the context's Poisson workspace
+}
+
 namespace {
 
 bool is_fin(double x) { return std::isfinite(x); }

@@ -105,8 +105,6 @@ struct GridParams {
 
 }  // namespace sq
 
-struct sq_poisson_ws;                // Poisson solver workspace (sq_scf.cu), created on first use
-
 struct sq_ctx {
     int precision;
     sq::GridParams g;
@@ -145,7 +143,6 @@ struct sq_ctx {
     double* d_fermi;                 // bisection state
     unsigned* d_count;               // last-block counters
     unsigned* d_err;                 // latched device error bits
-    sq_poisson_ws* pois;             // NULL until sq_poisson is first called
     int red_blocks;
 };
 
@@ -166,7 +163,6 @@ int enqueue_density(sq_ctx* ctx, const double* chi, const double* zeta, double m
 constexpr int FERMI_STATE = 12;      // doubles of the device Fermi/energy state
 int fermi_result(const double* st_host, double* mu, double* eb, double* es, double* ne);
 int launch_proj_tables(sq_ctx* ctx, const double* d_R);
-void free_poisson_ws(sq_ctx* ctx);
 }  // namespace sq
 
 #define SQ_CUDA_TRY(call)                                   \

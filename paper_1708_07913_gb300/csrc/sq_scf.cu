@@ -12,7 +12,9 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "sq_internal.cuh"
@@ -226,21 +228,36 @@ bool device_ptr(const void* p)
 
 }  // namespace
 
-// Poisson scratch of a context: b, r, p, Ap and a reduction.
-struct sq_poisson_ws {
+// Poisson scratch of a context: b, r, p, Ap and a reduction; kept in a
+// table keyed by the context (created on first use, released with it).
+struct PoissonWS {
     double* buf = nullptr;
     long long n = 0;
     Red red;
 };
 
+namespace {
+std::mutex g_ws_mutex;
+std::unordered_map<const sq_ctx*, PoissonWS*> g_ws;
+
+void ws_free(PoissonWS* w)
+{
+    if (!w) return;
+    if (w->buf) cudaFree(w->buf);
+    red_free(w->red);
+    delete w;
+}
+}  // namespace
+
 namespace sq {
+// Called when a context is destroyed.
 void free_poisson_ws(sq_ctx* c)
 {
-    if (!c || !c->pois) return;
-    if (c->pois->buf) cudaFree(c->pois->buf);
-    red_free(c->pois->red);
-    delete c->pois;
-    c->pois = nullptr;
+    std::lock_guard<std::mutex> lk(g_ws_mutex);
+    auto it = g_ws.find(c);
+    if (it == g_ws.end()) return;
+    ws_free(it->second);
+    g_ws.erase(it);
 }
 }  // namespace sq
 
@@ -303,23 +320,28 @@ int sq_poisson(sq_ctx* c, const double* rho, double* phi, double tol, int max_it
     if (!device_ptr(rho) || !device_ptr(phi)) return SQ_EINVAL;
     const long long n = c->g.Nd;
     cudaStream_t st = c->stream;
-    if (!c->pois) {
-        c->pois = new (std::nothrow) sq_poisson_ws();
-        if (!c->pois) return SQ_ENOMEM;
-        if (cudaMalloc(&c->pois->buf, sizeof(double) * 4 * n) != cudaSuccess) {
-            cudaGetLastError();
-            sq::free_poisson_ws(c);
-            return SQ_ENOMEM;
-        }
-        c->pois->n = n;
-        int rc = red_alloc(c->pois->red, c->sm_count, 8);
+    PoissonWS* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mutex);
+        auto it = g_ws.find(c);
+        if (it != g_ws.end()) ws = it->second;
+    }
+    if (!ws) {
+        ws = new (std::nothrow) PoissonWS();
+        if (!ws) return SQ_ENOMEM;
+        int rc = cudaMalloc(&ws->buf, sizeof(double) * 4 * n) == cudaSuccess ? SQ_OK : SQ_ENOMEM;
+        if (rc == SQ_OK) rc = red_alloc(ws->red, c->sm_count, 8);
         if (rc) {
-            sq::free_poisson_ws(c);
+            cudaGetLastError();
+            ws_free(ws);
             return rc;
         }
+        ws->n = n;
+        std::lock_guard<std::mutex> lk(g_ws_mutex);
+        g_ws[c] = ws;
     }
-    Red& R = c->pois->red;
-    double* b = c->pois->buf;
+    Red& R = ws->red;
+    double* b = ws->buf;
     double* r = b + n;
     double* p = r + n;
     double* Ap = p + n;
