@@ -71,6 +71,7 @@ def _load():
             lib.or_fermi_level.argtypes = [C.c_long, C.c_int, dp, dp, dp, C.c_double, C.c_double, dp, ip]
             lib.or_density_energy.argtypes = [C.c_long, C.c_int, dp, dp, dp, C.c_double, C.c_double,
                                               C.c_double, dp, dp, dp, dp]
+            lib.or_nl_force.argtypes = [sp, C.c_long, lp, dp, dp, C.c_int, C.c_double, C.c_double, dp]
             lib.or_laplacian_periodic.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp]
             lib.or_poisson_cg.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp, C.c_double,
                                           C.c_int, ip, dp]
@@ -163,6 +164,17 @@ class OracleSystem:
         if rc:
             raise ValueError("or_bounds failed")
         return chi, zeta
+
+    def nl_force(self, nodes, chi, zeta, npl, mu, kT):
+        """Nonlocal atomic forces (n_atoms x 3) summed over the given nodes
+        (Eq. Discrete:NLforce with the recurrence of Eq. Rec:FD1 to n_pl)."""
+        nodes = np.ascontiguousarray(nodes, dtype=np.int64)
+        chi, zeta = _f64(chi), _f64(zeta)
+        F = np.zeros((max(self.R.shape[0], 1), 3))
+        if _load().or_nl_force(C.byref(self._s), nodes.size, nodes.ctypes.data_as(C.POINTER(C.c_long)), _dp(chi),
+                               _dp(zeta), int(npl), float(mu), float(kT), _dp(F)) != 0:
+            raise ValueError("bad arguments")
+        return F[:self.R.shape[0]]
 
     def moments(self, nodes, chi, zeta, npl, product_rule=True):
         nodes = np.ascontiguousarray(nodes, dtype=np.int64)

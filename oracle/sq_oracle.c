@@ -76,6 +76,7 @@ typedef struct {
     int *idx;                /* region point indices             */
     double *val;             /* projector values chi(x)          */
     double gamma;            /* KB energy                        */
+    int atom;                /* atom the projector belongs to    */
 } or_proj;
 
 typedef struct {
@@ -112,7 +113,7 @@ static double proj_value(int l, int comp, double rc, double dx, double dy, doubl
     return Ap * ra * g;
 }
 
-static void op_add_proj(or_op *op, int npts, const int *idx, const double *val, double gamma)
+static void op_add_proj(or_op *op, int npts, const int *idx, const double *val, double gamma, int atom)
 {
     op->proj = (or_proj *)realloc(op->proj, sizeof(or_proj) * (op->nproj + 1));
     or_proj *p = &op->proj[op->nproj++];
@@ -122,6 +123,7 @@ static void op_add_proj(or_op *op, int npts, const int *idx, const double *val, 
     memcpy(p->idx, idx, sizeof(int) * npts);
     memcpy(p->val, val, sizeof(double) * npts);
     p->gamma = gamma;
+    p->atom = atom;
 }
 
 static void op_free(or_op *op)
@@ -190,7 +192,7 @@ static or_op *op_build(const or_sys *s, long q)
                     int np = 0;
                     for (long p = 0; p < op->Ns; ++p)
                         if (dense[p] != 0.0) { tidx[np] = (int)p; tval[np] = dense[p]; ++np; }
-                    op_add_proj(op, np, tidx, tval, gam);
+                    op_add_proj(op, np, tidx, tval, gam, I);
                 } else {
                     /* image shifts e for which the support box [lo+e n, hi+e n] meets */
                     /* the region [o, o+S-1] along every axis                          */
@@ -221,7 +223,7 @@ static or_op *op_build(const or_sys *s, long q)
                                         }
                                     }
                                 }
-                                if (np > 0) op_add_proj(op, np, tidx, tval, gam);
+                                if (np > 0) op_add_proj(op, np, tidx, tval, gam, I);
                             }
                 }
             }
@@ -596,5 +598,108 @@ int or_density_energy(long nq, int npl, const double *W, const double *chi, cons
         ne += h3 * rho[t];
     }
     *e_band = eb; *e_ent = es; *n_elec = ne;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Nonlocal component of the atomic force (Section 3.4, Eq. Discrete:NLforce */
+/* with the recurrence of Eq. Rec:FD1 run to n_pl):                           */
+/*   f_I^nl = -4 sum_q sum_{p of atom I} gamma_p h^3 chi_p(q) chi_p^T grad_h D_q */
+/* D_q = sum_{j=0}^{npl} c^j t^j (t^0 = e_q, t^1 = Hhat e_q, t^{j+1} = 2 Hhat  */
+/* t^j - t^{j-1}), the node's column of the density matrix in its region;     */
+/* c^j the Chebyshev interpolation coefficients of the Fermi-Dirac function   */
+/* g((chi_q + zeta_q x - mu)/kT) at the npl+1 zeros x_k (c^0 halved, the      */
+/* discrete orthogonality of the density calculation); grad_h the central     */
+/* finite-difference gradient of Eq. FD:Gradient inside the region (zero      */
+/* outside it; wrapped in periodic mode).  V_nl^{I'} = gamma h^3 chi chi^T    */
+/* per projector, every image of the atom included.  Adds into F[3*I+a].      */
+/* ------------------------------------------------------------------------ */
+static void grad_apply(const or_op *op, const double *wt, int axis, const double *x, double *y)
+{
+    int S1 = op->S1, S2 = op->S2, S3 = op->S3;
+    for (int c = 0; c < S3; ++c)
+        for (int b = 0; b < S2; ++b)
+            for (int a = 0; a < S1; ++a) {
+                double acc = 0.0;
+                for (int d = 1; d <= op->no; ++d) {
+                    int pa = a, pb = b, pc = c, ma = a, mb = b, mc = c;
+                    if (axis == 0) { pa += d; ma -= d; }
+                    else if (axis == 1) { pb += d; mb -= d; }
+                    else { pc += d; mc -= d; }
+                    double xp = 0.0, xm = 0.0;
+                    if (op->periodic) {
+                        xp = x[wrap(pa, S1) + S1 * (wrap(pb, S2) + S2 * wrap(pc, S3))];
+                        xm = x[wrap(ma, S1) + S1 * (wrap(mb, S2) + S2 * wrap(mc, S3))];
+                    } else {
+                        if (pa < S1 && pb < S2 && pc < S3) xp = x[pa + S1 * (pb + S2 * pc)];
+                        if (ma >= 0 && mb >= 0 && mc >= 0) xm = x[ma + S1 * (mb + S2 * mc)];
+                    }
+                    acc += wt[d] * (xp - xm);
+                }
+                y[a + S1 * (b + S2 * c)] = acc;
+            }
+}
+
+int or_nl_force(const or_sys *s, long nq, const long *nodes, const double *chi, const double *zeta, int npl,
+                double mu, double kT, double *F)
+{
+    if (npl < 1 || !(kT > 0.0)) return 1;
+    const int no = s->no;
+    double wt[OR_MAX_NO + 1];
+    for (int d = 1; d <= no; ++d) {
+        double sign = (d % 2 == 1) ? 1.0 : -1.0;             /* (-1)^{d+1} */
+        wt[d] = sign / (s->h * d) * factorial(no) * factorial(no) / (factorial(no - d) * factorial(no + d));
+    }
+    const double h3 = s->h * s->h * s->h;
+    double *c = (double *)malloc(sizeof(double) * (npl + 1));
+    for (long iq = 0; iq < nq; ++iq) {
+        or_op *op = op_build(s, nodes[iq]);
+        const long N = op->Ns, ctr = op->centre;
+        /* projectors that are non-zero at the node */
+        int any = 0;
+        for (int p = 0; p < op->nproj; ++p)
+            for (int k = 0; k < op->proj[p].npts; ++k)
+                if (op->proj[p].idx[k] == ctr) any = 1;
+        if (!any) { op_free(op); continue; }
+        /* c^j by discrete orthogonality at the zeros of T_{npl+1} */
+        for (int j = 0; j <= npl; ++j) {
+            double acc = 0.0;
+            for (int k = 0; k <= npl; ++k) {
+                double x = or_cheb_node(npl, k);
+                acc += fermi(chi[iq] + zeta[iq] * x, mu, kT) * cos(j * acos(x));
+            }
+            c[j] = 2.0 / (npl + 1) * acc;
+        }
+        c[0] *= 0.5;
+        double *tm = (double *)calloc(N, sizeof(double)), *t = (double *)calloc(N, sizeof(double));
+        double *tn = (double *)malloc(sizeof(double) * N), *D = (double *)calloc(N, sizeof(double));
+        double *g = (double *)malloc(sizeof(double) * N);
+        tm[ctr] = 1.0;                                        /* t^0 = e_q */
+        hhat_apply(op, chi[iq], zeta[iq], tm, t);             /* t^1       */
+        for (long i = 0; i < N; ++i) D[i] = c[0] * tm[i] + (npl >= 1 ? c[1] * t[i] : 0.0);
+        for (int j = 2; j <= npl; ++j) {
+            hhat_apply(op, chi[iq], zeta[iq], t, tn);
+            for (long i = 0; i < N; ++i) {
+                tn[i] = 2.0 * tn[i] - tm[i];
+                D[i] += c[j] * tn[i];
+            }
+            double *tmp = tm; tm = t; t = tn; tn = tmp;
+        }
+        for (int axis = 0; axis < 3; ++axis) {
+            grad_apply(op, wt, axis, D, g);
+            for (int p = 0; p < op->nproj; ++p) {
+                const or_proj *pr = &op->proj[p];
+                double chi_q = 0.0, proj = 0.0;
+                for (int k = 0; k < pr->npts; ++k) {
+                    if (pr->idx[k] == ctr) chi_q = pr->val[k];
+                    proj += pr->val[k] * g[pr->idx[k]];
+                }
+                F[3 * pr->atom + axis] -= 4.0 * pr->gamma * h3 * chi_q * proj;
+            }
+        }
+        free(tm); free(t); free(tn); free(D); free(g);
+        op_free(op);
+    }
+    free(c);
     return 0;
 }
