@@ -174,6 +174,29 @@ int sq_density_energy_noalloc(int n1, int n2, int n3, double h, int npl,
                               double *e_band_host, double *e_ent_host, double *n_elec_host,
                               void *cuda_stream);
 
+/* Nonlocal component of the atomic forces (Section 3.4, Eq. Discrete:NLforce,
+ * with the recurrence of Eq. Rec:FD1 run to n_pl):
+ *   f_I = -4 sum_q sum_{p of atom I} gamma_p h^3 chi_p(q) chi_p^T grad_h D_q,
+ *   D_q = sum_{j=0}^{npl} c_q^j t^j   (t^j as for sq_moments, run to npl),
+ * c_q^j the Chebyshev coefficients of the Fermi-Dirac function at mu, kT on
+ * [chi_q - zeta_q, chi_q + zeta_q] (discrete orthogonality at the npl+1
+ * zeros of T_{npl+1}, c^0 halved), grad_h the central finite-difference
+ * gradient of Eq. FD:Gradient (order n_o) inside the node's region, zero
+ * outside it.  Every periodic image of every projector whose support meets
+ * the region enters, as in H_q; only nodes inside some projector's support
+ * contribute.
+ *   V          device, N_d FP64 (the potential the bounds were computed for)
+ *   chi, zeta  device, N_d FP64 (from sq_spectral_bounds)
+ *   mu, kT     Fermi level (e.g. from sq_fermi_level) and smearing > 0, Ha
+ *   forces     device, n_atoms*3 FP64 output (Ha/bohr, atom-major x,y,z),
+ *              overwritten; may be NULL when the context has no projectors
+ * FP64 contexts only (SQ_EUNSUPPORTED otherwise).  The result repeats bit for
+ * bit on a given GPU.  Allocates, on first use, about 2 x SMs x (32 (2m+1)^3
+ * + 52 ccap + 24 n_atoms) bytes of workspace in the context.  Synchronises
+ * the stream; a projector-table overflow returns SQ_ECAPACITY. */
+int sq_nl_forces(sq_ctx *ctx, const double *V, const double *chi, const double *zeta,
+                 double mu, double kT, double *forces);
+
 /* ---------------------------------------------------------------------------
  * Batch of independent systems.  The paper treats one system at a time (its
  * parallelism is over the nodes of one grid, Section 3.2); it has no
@@ -273,6 +296,63 @@ int sq_mixer_export(sq_mixer *mx, double *X_host, double *F_host);
 int sq_mixer_import(sq_mixer *mx, int count, const double *X_host, const double *F_host);
 int sq_mixer_reset(sq_mixer *mx);
 void sq_mixer_destroy(sq_mixer *mx);
+
+/* ---------------------------------------------------------------------------
+ * Learned SCF warm start.  The paper has no counterpart.  A small 3-D
+ * convolutional network, trained on densities the SQ path itself produces,
+ * maps the 9^3 patch of the effective potential around each node to the
+ * node's density, so that an SCF can start from a predicted density
+ * instead of the bare local potential.  On the periodic n1 x n2 x n3 grid:
+ *   x0  = (V - v_shift) / v_scale
+ *   a1  = silu(conv5(x0; W1) + b1)     1 -> 32 channels, 5^3 kernel
+ *   a2  = silu(conv3(a1; W2) + b2)     32 -> 32 channels, 3^3 kernel
+ *   y   = conv3(a2; W3) + b3           32 -> 1 channel, 3^3 kernel
+ *   rho = rho_scale * softplus(y)
+ * with conv_k(x; W)[o](p) = sum_i sum_{d in [-r,r]^3} W[o,i,d] x[i](p + d)
+ * (periodic cross-correlation, r = (k-1)/2), silu(z) = z/(1 + e^-z),
+ * softplus(y) = log(1 + e^y); loss = mean((rho - rho_ref)^2) / rho_scale^2.
+ * Weights and activations are stored in bfloat16 (bf16 = 1) or FP32
+ * (bf16 = 0), every sum accumulates in FP32, and the master weights,
+ * biases, gradients and Adam moments are FP32.  Results repeat bit for bit.
+ *
+ * Parameters travel as one HOST array of FP64 in the network's natural
+ * order: W1 (32,1,5,5,5), b1 (32), W2 (32,32,3,3,3), b2 (32), W3 (1,32,3,3,3),
+ * b3 (1), each C-ordered with the kernel axes (dz, dy, dx) -- 32,577 values
+ * (sq_cnn_param_count(32)).
+ *
+ * sq_cnn_create(out, channels, bf16, cuda_stream): channels must be 32
+ *   (SQ_EUNSUPPORTED otherwise).  Allocates the weights; activation buffers
+ *   grow on first use with a grid (about 4 N (3 C s + 4 C + 5) bytes for N
+ *   nodes, s = 2 or 4 bytes of storage, plus the weight-gradient partials).
+ * sq_cnn_set_params(net, params_host, v_shift, v_scale, rho_scale): load
+ *   weights (rounded to FP32), input shift/scale (v_scale != 0) and output
+ *   scale (> 0); resets the Adam state.  sq_cnn_get_params: read them back.
+ * sq_cnn_forward(net, n1, n2, n3, V, rho): V, rho device N FP64.
+ * sq_cnn_backward(net, n1, n2, n3, V, rho_ref, rho, accumulate, loss_host):
+ *   forward into rho, the loss against rho_ref (all device N FP64) into
+ *   loss_host (HOST, may be NULL; synchronises when given), and the
+ *   gradient of the loss with respect to every parameter, stored in the net
+ *   (accumulate = 1 adds it to the stored gradient, e.g. over a batch of
+ *   systems).  sq_cnn_get_grads(net, grads_host): read it (natural order).
+ * sq_cnn_adam_step(net, lr, beta1, beta2, eps, grad_scale): one Adam step
+ *   (Kingma and Ba) on the stored gradient times grad_scale:
+ *   m = b1 m + (1-b1) g, v = b2 v + (1-b2) g^2,
+ *   w -= lr (m / (1 - b1^t)) / (sqrt(v / (1 - b2^t)) + eps).
+ * sq_cnn_destroy(net): release (NULL: no-op).
+ * Grids up to 2^28 nodes, each edge 1..4096; argument errors SQ_EINVAL.
+ * ------------------------------------------------------------------------- */
+typedef struct sq_cnn sq_cnn;
+long long sq_cnn_param_count(int channels);
+int sq_cnn_create(sq_cnn **out, int channels, int bf16, void *cuda_stream);
+int sq_cnn_set_params(sq_cnn *net, const double *params_host, double v_shift, double v_scale,
+                      double rho_scale);
+int sq_cnn_get_params(sq_cnn *net, double *params_host);
+int sq_cnn_forward(sq_cnn *net, int n1, int n2, int n3, const double *V, double *rho);
+int sq_cnn_backward(sq_cnn *net, int n1, int n2, int n3, const double *V, const double *rho_ref,
+                    double *rho, int accumulate, double *loss_host);
+int sq_cnn_get_grads(sq_cnn *net, double *grads_host);
+int sq_cnn_adam_step(sq_cnn *net, double lr, double beta1, double beta2, double eps, double grad_scale);
+void sq_cnn_destroy(sq_cnn *net);
 
 /* Wait for the context's stream and return any latched device error. */
 int sq_sync(sq_ctx *ctx);

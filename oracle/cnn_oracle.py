@@ -140,15 +140,30 @@ def init_params(seed: int, channels: int = CHANNELS, v_shift: float = 0.0, v_sca
 TRAINED = ("W1", "b1", "W2", "b2", "W3", "b3")
 
 
-def forward(params, V):
-    """rho (n3, n2, n1) and the activations the backward pass needs."""
-    x0 = ((np.asarray(V, dtype=np.float64) - params["v_shift"]) / params["v_scale"])[None]
-    z1 = conv(x0, params["W1"], params["b1"])
-    a1 = silu(z1)
-    z2 = conv(a1, params["W2"], params["b2"])
-    a2 = silu(z2)
-    y = conv(a2, params["W3"], params["b3"])
-    rho = params["rho_scale"] * softplus(y[0])
+def _stored(params, bf16):
+    """The weights as the network applies them: bf16-rounded when the
+    weights and activations are stored in bfloat16."""
+    if not bf16:
+        return params
+    q = dict(params)
+    for k in ("W1", "W2", "W3"):
+        q[k] = to_bf16(params[k])
+    return q
+
+
+def forward(params, V, bf16=False):
+    """rho (n3, n2, n1) and the activations the backward pass needs.  With
+    bf16=True, the weights, x0, a1 and a2 are rounded to bfloat16 where they
+    are stored (everything else stays FP64)."""
+    rnd = to_bf16 if bf16 else (lambda a: a)
+    p = _stored(params, bf16)
+    x0 = rnd(((np.asarray(V, dtype=np.float64) - p["v_shift"]) / p["v_scale"])[None])
+    z1 = conv(x0, p["W1"], p["b1"])
+    a1 = rnd(silu(z1))
+    z2 = conv(a1, p["W2"], p["b2"])
+    a2 = rnd(silu(z2))
+    y = conv(a2, p["W3"], p["b3"])
+    rho = p["rho_scale"] * softplus(y[0])
     return rho, dict(x0=x0, z1=z1, a1=a1, z2=z2, a2=a2, y=y)
 
 
@@ -157,9 +172,13 @@ def loss(params, V, rho_ref):
     return float(np.mean((rho - rho_ref) ** 2) / params["rho_scale"] ** 2)
 
 
-def backward(params, V, rho_ref):
-    """Loss and its gradient with respect to every trained parameter."""
-    rho, c = forward(params, V)
+def backward(params, V, rho_ref, bf16=False):
+    """Loss and its gradient with respect to every trained parameter.  With
+    bf16=True the backward pass of the rounded network takes the stored
+    (rounded) weights and activations and treats the rounding as the
+    identity."""
+    rho, c = forward(params, V, bf16)
+    params = _stored(params, bf16)
     N = rho.size
     rs = params["rho_scale"]
     L = float(np.mean((rho - rho_ref) ** 2) / rs ** 2)

@@ -13,7 +13,8 @@ from __future__ import annotations
 from . import sq
 from .sq import SQ_FP32, SQ_FP64, SQError
 
-__all__ = ["sq", "SQSolver", "SQBatch", "SQSCF", "SQ_FP32", "SQ_FP64", "SQError", "build"]
+__all__ = ["sq", "SQSolver", "SQBatch", "SQSCF", "SQCNN", "warm_start_potential", "SQ_FP32", "SQ_FP64",
+           "SQError", "build"]
 
 
 def build(force: bool = False) -> str:
@@ -34,6 +35,7 @@ class SQSolver:
         self.h = float(h)
         n1, n2, n3 = self.shape
         self.n_nodes = n1 * n2 * n3
+        self.n_atoms = len(positions) if (positions is not None and len(proj_types)) else 0
         with torch.cuda.device(self.device):
             self.ctx = sq.sq_setup_grid(n1, n2, n3, h, fd_half_order, r_cut, npl, precision, positions,
                                         list(proj_types))
@@ -80,6 +82,14 @@ class SQSolver:
         sq.sq_set_stream(self.ctx)
         return sq.sq_density_energy(self.ctx, self.moments, self.chi if chi is None else chi,
                                     self.zeta if zeta is None else zeta, mu, kT, self.rho)
+
+    def nl_forces(self, V, mu, kT, chi=None, zeta=None):
+        """Nonlocal atomic forces (n_atoms, 3), Ha/bohr, at Fermi level mu."""
+        F = self.torch.zeros(max(self.n_atoms, 1) * 3, dtype=self.torch.float64, device=self.device)
+        sq.sq_set_stream(self.ctx)
+        sq.sq_nl_forces(self.ctx, V, self.chi if chi is None else chi, self.zeta if zeta is None else zeta, mu, kT,
+                        F if self.n_atoms else None)
+        return F[:3 * self.n_atoms].view(self.n_atoms, 3)
 
     def solve(self, V, n_electrons, kT, n_lanczos=40, margin=0.01, bounds=None):
         """The whole path on a device potential V (float64, N_d).  ``bounds``
@@ -156,13 +166,15 @@ class SQSCF:
         with torch.cuda.device(solver.device):
             self.mixer = sq.sq_mixer_create(solver.n_nodes, history, beta)
 
-    def run(self, V0=None, tol=1e-6, max_iter=60, poisson_tol=1e-12, checkpoint=None, resume=None):
+    def run(self, V0=None, tol=1e-6, max_iter=60, poisson_tol=1e-12, checkpoint=None, resume=None, on_step=None):
         """Returns a dict: V (the converged input potential), rho, mu,
         e_band, e_ent, n_elec, residuals, iterations, converged, poisson
         iterations per SCF step.  ``checkpoint``: a path; after every
         iteration the next input potential and the mixing history are saved
         there (.npz of .npy arrays).  ``resume``: such a file; the loop
-        continues from it (V0 is then ignored)."""
+        continues from it (V0 is then ignored).  ``on_step(V_in, rho)`` is
+        called after every SQ solve (e.g. to collect training pairs; the
+        tensors are reused by the next iteration)."""
         import numpy as np
         sv = self.solver
         sq.sq_mixer_reset(self.mixer)
@@ -177,6 +189,8 @@ class SQSCF:
             V_in.copy_(self.V_loc if V0 is None else V0)
         for it in range(len(res), max_iter):
             out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
+            if on_step is not None:
+                on_step(V_in, sv.rho)
             sq.sq_set_stream(sv.ctx)
             k, _ = sq.sq_poisson(sv.ctx, sv.rho, self.phi, poisson_tol)
             pit.append(k)
@@ -204,3 +218,102 @@ class SQSCF:
             self.close()
         except Exception:
             pass
+
+
+class SQCNN:
+    """The learned warm start's network (sq_cnn_*, include/sq.h): a 3-D CNN
+    on the periodic grid mapping the 9^3 patch of the effective potential
+    around each node to the node's SQ density.  Weights and activations in
+    bfloat16 (or FP32), FP32 accumulation, FP32 master weights and Adam
+    state; every step runs in libsq."""
+
+    CHANNELS = 32
+    KERNELS = (5, 3, 3)
+
+    def __init__(self, bf16=True, seed=0, v_shift=-1.0, v_scale=1.0, rho_scale=0.03, device="cuda:0"):
+        import numpy as np
+        import torch
+        self.torch, self.device, self.bf16 = torch, torch.device(device), bool(bf16)
+        with torch.cuda.device(self.device):
+            self.net = sq.sq_cnn_create(self.CHANNELS, self.bf16)
+        C, (k1, k2, k3) = self.CHANNELS, self.KERNELS
+        rng = np.random.default_rng(seed)            # variance 1/fan-in, zero biases
+        parts = [rng.standard_normal(C * k1 ** 3) / np.sqrt(k1 ** 3), np.zeros(C),
+                 rng.standard_normal(C * C * k2 ** 3) / np.sqrt(C * k2 ** 3), np.zeros(C),
+                 rng.standard_normal(C * k3 ** 3) / np.sqrt(C * k3 ** 3), np.zeros(1)]
+        self.set_params(np.concatenate(parts), v_shift, v_scale, rho_scale)
+
+    def set_params(self, flat, v_shift, v_scale, rho_scale):
+        self.scales = (float(v_shift), float(v_scale), float(rho_scale))
+        sq.sq_cnn_set_params(self.net, flat, *self.scales)
+
+    def params(self):
+        return sq.sq_cnn_get_params(self.net)
+
+    def predict(self, shape, V, out=None):
+        """Density (float64, N) of the potential V (device float64, N) on the periodic grid ``shape`` = (n1, n2, n3)."""
+        rho = out if out is not None else self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
+        sq.sq_cnn_forward(self.net, shape, V, rho)
+        return rho
+
+    def train_step(self, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+        """One Adam step on the mean loss over ``batch`` = [(shape, V, rho_ref), ...]; returns that mean loss."""
+        total = 0.0
+        for i, (shape, V, ref) in enumerate(batch):
+            rho = self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
+            total += sq.sq_cnn_backward(self.net, shape, V, ref, rho, accumulate=i > 0)
+        sq.sq_cnn_adam_step(self.net, lr, beta1, beta2, eps, grad_scale=1.0 / len(batch))
+        return total / len(batch)
+
+    def save(self, path):
+        import numpy as np
+        np.savez(path, params=self.params(), scales=np.array(self.scales), bf16=np.array(self.bf16))
+
+    @classmethod
+    def load(cls, path, device="cuda:0"):
+        import numpy as np
+        d = np.load(path)
+        net = cls(bool(d["bf16"]), 0, *d["scales"], device=device)
+        net.set_params(d["params"], *d["scales"])
+        return net
+
+    def close(self):
+        if getattr(self, "net", None):
+            sq.sq_cnn_destroy(self.net)
+            self.net = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4, beta=0.3, history=7,
+                         poisson_tol=1e-10):
+    """The SCF's starting potential from the learned network: the fixed
+    point of V_in -> rho = net(V_in) -> V_out = V_loc + phi[rho] + v_x(rho)
+    (the SCF map with the network in place of the SQ solve, Anderson-mixed,
+    at most ``iters`` steps or until ||V_out - V_in|| <= tol ||V_out||).
+    Returns (V_in, residuals); every step runs in libsq."""
+    torch = solver.torch
+    shape = solver.shape
+    f64 = dict(dtype=torch.float64, device=solver.device)
+    V_in, V_next = V_loc.clone(), torch.empty(solver.n_nodes, **f64)
+    rho, phi, V_out = (torch.empty(solver.n_nodes, **f64) for _ in range(3))
+    with torch.cuda.device(solver.device):
+        mixer = sq.sq_mixer_create(solver.n_nodes, history, beta)
+    res = []
+    try:
+        sq.sq_set_stream(solver.ctx)
+        for _ in range(iters):
+            net.predict(shape, V_in, out=rho)
+            sq.sq_poisson(solver.ctx, rho, phi, poisson_tol)
+            sq.sq_effective_potential(solver.ctx, V_loc, phi, rho, alpha, V_out)
+            res.append(sq.sq_mixer_step(mixer, V_in, V_out, V_next))
+            V_in, V_next = V_next, V_in
+            if res[-1] <= tol:
+                break
+    finally:
+        sq.sq_mixer_destroy(mixer)
+    return V_in, res

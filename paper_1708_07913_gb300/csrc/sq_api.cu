@@ -23,6 +23,7 @@ using namespace sq;
 
 namespace sq {
 void free_poisson_ws(sq_ctx* ctx);   // sq_scf.cu: the context's Poisson workspace
+void free_force_ws(sq_ctx* ctx);     // sq_force.cu: the context's force workspace
 }
 
 namespace {
@@ -77,6 +78,7 @@ void free_ctx(sq_ctx* c)
     for (void* p : ptrs)
         if (p) cudaFree(p);
     free_poisson_ws(c);
+    free_force_ws(c);
     delete c;
 }
 

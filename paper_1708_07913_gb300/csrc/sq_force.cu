@@ -1,0 +1,193 @@
+// sq_force.cu -- host side of sq_nl_forces (include/sq.h): argument checks,
+// the per-context force workspace, and the two launches (the per-node force
+// kernel of sq_force.cuh and the fixed-order sum over its CTAs).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+
+#include "sq_force.cuh"
+
+using namespace sq;
+
+namespace sq {
+int launch_build_vpad(sq_ctx* ctx, const double* V);
+}
+
+// Per-context scratch of the force kernel (created on first use, grown when
+// needed, released with the context).
+struct ForceWS {
+    char* buf = nullptr;
+    size_t bytes = 0;
+    int blocks = 0;
+};
+
+namespace {
+
+std::mutex g_force_mutex;
+std::unordered_map<const sq_ctx*, ForceWS*> g_force_ws;
+
+bool dev_ptr(const void* p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Byte offsets of the per-CTA slices inside one CTA's part of the workspace.
+struct ForceLayout {
+    size_t vec, cand, clen, P, F, total;
+};
+
+ForceLayout force_layout(int S, int cap, int n_atoms)
+{
+    ForceLayout L;
+    const size_t S3 = (size_t)S * S * S;
+    L.vec = 0;
+    L.cand = L.vec + align256(sizeof(double) * 4 * S3);
+    L.clen = L.cand + align256(sizeof(int4) * cap);
+    L.P = L.clen + align256(sizeof(int) * cap);
+    L.F = L.P + align256(sizeof(double) * 4 * cap);
+    L.total = L.F + align256(sizeof(double) * 3 * (size_t)n_atoms);
+    return L;
+}
+
+// The central finite-difference gradient weights of Eq. (FD:Gradient):
+//   wt_d = (-1)^{d+1} (n_o!)^2 / (h d (n_o-d)! (n_o+d)!),  d = 1..n_o.
+void grad_weights(int no, double h, double* wt)
+{
+    double f[32];
+    f[0] = 1.0;
+    for (int i = 1; i < 32; ++i) f[i] = f[i - 1] * i;
+    wt[0] = 0.0;
+    for (int d = 1; d <= no; ++d) wt[d] = ((d & 1) ? 1.0 : -1.0) / (h * d) * f[no] * f[no] / (f[no - d] * f[no + d]);
+}
+
+void ws_release(ForceWS* w)
+{
+    if (!w) return;
+    if (w->buf) cudaFree(w->buf);
+    delete w;
+}
+
+}  // namespace
+
+namespace sq {
+// Called when a context is destroyed.
+void free_force_ws(sq_ctx* c)
+{
+    std::lock_guard<std::mutex> lk(g_force_mutex);
+    auto it = g_force_ws.find(c);
+    if (it == g_force_ws.end()) return;
+    ws_release(it->second);
+    g_force_ws.erase(it);
+}
+}  // namespace sq
+
+extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta, double mu, double kT,
+                            double* forces)
+{
+    if (!c || !isfinite(mu) || !isfinite(kT) || kT <= 0.0) return SQ_EINVAL;
+    if (!dev_ptr(V) || !dev_ptr(chi) || !dev_ptr(zeta)) return SQ_EINVAL;
+    if (c->n_atoms > 0 && !dev_ptr(forces)) return SQ_EINVAL;
+    if (c->precision != SQ_FP64) return SQ_EUNSUPPORTED;
+    if (c->n_atoms == 0) return SQ_OK;
+    const int n3 = 3 * c->n_atoms;
+    if (!c->has_s && !c->has_p)
+        return cudaMemsetAsync(forces, 0, sizeof(double) * n3, c->stream) == cudaSuccess ? SQ_OK : SQ_ECUDA;
+
+    const int S = 2 * c->g.m + 1;
+    const ForceLayout L = force_layout(S, c->ccap, c->n_atoms);
+    const int blocks = (int)std::min<long long>(c->g.Nd, 2LL * c->sm_count);
+    const size_t need = L.total * (size_t)blocks;
+    ForceWS* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_force_mutex);
+        auto it = g_force_ws.find(c);
+        if (it != g_force_ws.end()) ws = it->second;
+    }
+    if (!ws || ws->bytes < need) {
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+        std::lock_guard<std::mutex> lk(g_force_mutex);
+        auto it = g_force_ws.find(c);
+        if (it != g_force_ws.end()) {
+            ws_release(it->second);
+            g_force_ws.erase(it);
+        }
+        ws = new (std::nothrow) ForceWS();
+        if (!ws) return SQ_ENOMEM;
+        if (cudaMalloc((void**)&ws->buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            ws_release(ws);
+            return SQ_ENOMEM;
+        }
+        ws->bytes = need;
+        g_force_ws[c] = ws;
+    }
+    ws->blocks = blocks;
+
+    int rc = launch_build_vpad(c, V);
+    if (rc) return rc;
+
+    // the per-CTA slices are interleaved by kind: all CTAs' vectors, then all
+    // candidate lists, ... (each kind contiguous, CTA b at offset b * size)
+    ForceArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = c->g;
+    a.lap[0] = -3.0 * c->g.w[0];
+    for (int d = 1; d <= FD_NO; ++d) a.lap[d] = -0.5 * c->g.w[d];
+    grad_weights(FD_NO, c->g.h, a.grad);
+    a.Vp = (const double*)c->Vp;
+    a.nl.n_atoms = c->n_atoms;
+    a.nl.atoms = c->d_atoms;
+    a.nl.lb = c->lb;
+    a.nl.G = (const double*)c->d_G;
+    a.nl.DG = (const double*)c->d_DG;
+    a.nl.ivl = c->d_ivl;
+    a.nl.tile_start = c->d_tile_start;
+    a.nl.tile_cand = c->d_tile_cand;
+    for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
+    a.nl.ccap = c->ccap;
+    a.nl.smem = 0;
+    const double h3 = c->g.h * c->g.h * c->g.h;
+    const double As2 = pow(M_PI * c->rc * c->rc, -1.5);          // A_s^2
+    const double Ap2 = 2.0 / (c->rc * c->rc) * As2;              // A_p^2
+    a.nl.cs = c->has_s ? h3 * c->gamma_s * As2 : 0.0;
+    a.nl.cp = c->has_p ? h3 * c->gamma_p * Ap2 : 0.0;
+    a.chi = chi;
+    a.zeta = zeta;
+    a.mu = mu;
+    a.kT = kT;
+    a.npl = c->npl;
+    char* base = ws->buf;
+    a.vec = (double*)(base + L.vec * blocks);
+    a.cand = (int4*)(base + L.cand * blocks);
+    a.clen = (int*)(base + L.clen * blocks);
+    a.P = (double*)(base + L.P * blocks);
+    a.Fcta = (double*)(base + L.F * blocks);
+    a.err = c->d_err;
+
+    nl_force_kernel<<<blocks, FORCE_NT, 0, c->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    force_sum_kernel<<<(n3 + 127) / 128, 128, 0, c->stream>>>(a.Fcta, blocks, n3, forces);
+    if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    c->launches += 2;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+    unsigned e = 0;
+    if (cudaMemcpy(&e, c->d_err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return SQ_ECUDA;
+    if (e) {
+        unsigned z = 0;
+        if (cudaMemcpy(c->d_err, &z, sizeof(z), cudaMemcpyHostToDevice) != cudaSuccess) return SQ_ECUDA;
+        return (e & ERR_CAPACITY) ? SQ_ECAPACITY : SQ_EBOUNDS;
+    }
+    return SQ_OK;
+}

@@ -25,7 +25,9 @@ EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments",
            "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
            "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
-           "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy")
+           "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
+           "sq_nl_forces", "sq_cnn_param_count", "sq_cnn_create", "sq_cnn_set_params", "sq_cnn_get_params",
+           "sq_cnn_forward", "sq_cnn_backward", "sq_cnn_get_grads", "sq_cnn_adam_step", "sq_cnn_destroy")
 
 
 class SQError(RuntimeError):
@@ -77,6 +79,18 @@ def load(path: str = LIB_PATH):
         lib.sq_batch_destroy.restype = None
         lib.sq_poisson.argtypes = [vp, vp, vp, C.c_double, ip, C.POINTER(ip), dp]
         lib.sq_effective_potential.argtypes = [vp, vp, vp, vp, C.c_double, vp]
+        lib.sq_nl_forces.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp]
+        lib.sq_cnn_param_count.argtypes = [ip]
+        lib.sq_cnn_param_count.restype = C.c_longlong
+        lib.sq_cnn_create.argtypes = [C.POINTER(vp), ip, ip, vp]
+        lib.sq_cnn_set_params.argtypes = [vp, dp, C.c_double, C.c_double, C.c_double]
+        lib.sq_cnn_get_params.argtypes = [vp, dp]
+        lib.sq_cnn_forward.argtypes = [vp, ip, ip, ip, vp, vp]
+        lib.sq_cnn_backward.argtypes = [vp, ip, ip, ip, vp, vp, vp, ip, dp]
+        lib.sq_cnn_get_grads.argtypes = [vp, dp]
+        lib.sq_cnn_adam_step.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
+        lib.sq_cnn_destroy.argtypes = [vp]
+        lib.sq_cnn_destroy.restype = None
         lib.sq_mixer_create.argtypes = [C.POINTER(vp), C.c_longlong, ip, C.c_double, vp]
         lib.sq_mixer_step.argtypes = [vp, vp, vp, vp, dp]
         lib.sq_mixer_history.argtypes = [vp, C.POINTER(ip)]
@@ -159,6 +173,12 @@ def sq_density_energy(ctx, moments, chi, zeta, mu, kT, rho):
                                     _dptr(zeta, "zeta"), float(mu), float(kT), _dptr(rho, "rho"),
                                     C.byref(eb), C.byref(es), C.byref(ne)), "sq_density_energy")
     return eb.value, es.value, ne.value
+
+
+def sq_nl_forces(ctx, V, chi, zeta, mu, kT, forces):
+    """forces: float64 CUDA tensor of n_atoms*3 (None when there are no projectors)."""
+    _check(load().sq_nl_forces(C.c_void_p(ctx), _dptr(V, "V"), _dptr(chi, "chi"), _dptr(zeta, "zeta"), float(mu),
+                               float(kT), _dptr(forces, "forces")), "sq_nl_forces")
 
 
 def sq_density_energy_noalloc(shape, h, npl, moments, chi, zeta, mu, kT, rho, stream=None):
@@ -287,3 +307,60 @@ def sq_mixer_reset(mixer):
 def sq_mixer_destroy(mixer):
     if mixer:
         load().sq_mixer_destroy(C.c_void_p(mixer))
+
+
+def sq_cnn_param_count(channels=32) -> int:
+    return int(load().sq_cnn_param_count(int(channels)))
+
+
+def sq_cnn_create(channels=32, bf16=True, stream=None):
+    net = C.c_void_p()
+    _check(load().sq_cnn_create(C.byref(net), int(channels), int(bool(bf16)),
+                                stream if stream is not None else _stream()), "sq_cnn_create")
+    return net.value
+
+
+def sq_cnn_set_params(net, params, v_shift, v_scale, rho_scale):
+    """params: flat float64 array in the network's natural order."""
+    p = np.ascontiguousarray(params, dtype=np.float64)
+    if p.size != sq_cnn_param_count():
+        raise ValueError("wrong parameter count")
+    _check(load().sq_cnn_set_params(C.c_void_p(net), p.ctypes.data_as(C.POINTER(C.c_double)), float(v_shift),
+                                    float(v_scale), float(rho_scale)), "sq_cnn_set_params")
+
+
+def sq_cnn_get_params(net):
+    p = np.zeros(sq_cnn_param_count())
+    _check(load().sq_cnn_get_params(C.c_void_p(net), p.ctypes.data_as(C.POINTER(C.c_double))), "sq_cnn_get_params")
+    return p
+
+
+def sq_cnn_forward(net, shape, V, rho):
+    n1, n2, n3 = shape
+    _check(load().sq_cnn_forward(C.c_void_p(net), int(n1), int(n2), int(n3), _dptr(V, "V"), _dptr(rho, "rho")),
+           "sq_cnn_forward")
+
+
+def sq_cnn_backward(net, shape, V, rho_ref, rho, accumulate=False, want_loss=True):
+    n1, n2, n3 = shape
+    L = C.c_double()
+    _check(load().sq_cnn_backward(C.c_void_p(net), int(n1), int(n2), int(n3), _dptr(V, "V"),
+                                  _dptr(rho_ref, "rho_ref"), _dptr(rho, "rho"), int(bool(accumulate)),
+                                  C.byref(L) if want_loss else None), "sq_cnn_backward")
+    return L.value if want_loss else None
+
+
+def sq_cnn_get_grads(net):
+    g = np.zeros(sq_cnn_param_count())
+    _check(load().sq_cnn_get_grads(C.c_void_p(net), g.ctypes.data_as(C.POINTER(C.c_double))), "sq_cnn_get_grads")
+    return g
+
+
+def sq_cnn_adam_step(net, lr, beta1=0.9, beta2=0.999, eps=1e-8, grad_scale=1.0):
+    _check(load().sq_cnn_adam_step(C.c_void_p(net), float(lr), float(beta1), float(beta2), float(eps),
+                                   float(grad_scale)), "sq_cnn_adam_step")
+
+
+def sq_cnn_destroy(net):
+    if net:
+        load().sq_cnn_destroy(C.c_void_p(net))

@@ -97,6 +97,27 @@ def test_calls_reject_null_context(lib):
     assert lib.sq_sync(None) == sq.SQ_EINVAL
     assert lib.sq_launch_count(None) == -1
     lib.sq_destroy(None)
+    assert lib.sq_nl_forces(None, None, None, None, 0.0, 0.1, None) == sq.SQ_EINVAL
+
+
+def test_cnn_host_checks(lib):
+    """Parameter count of the warm-start network and the checks made before
+    any CUDA call (no GPU needed)."""
+    from paper_1708_07913_gb300 import sq
+    from oracle import cnn_oracle
+    p = cnn_oracle.init_params(0)
+    assert lib.sq_cnn_param_count(32) == sum(p[k].size for k in cnn_oracle.TRAINED) == 32577
+    assert lib.sq_cnn_param_count(16) == -1
+    net = C.c_void_p()
+    assert lib.sq_cnn_create(C.byref(net), 16, 1, None) == sq.SQ_EUNSUPPORTED and not net.value
+    assert lib.sq_cnn_create(C.byref(net), 32, 2, None) == sq.SQ_EINVAL
+    assert lib.sq_cnn_create(None, 32, 1, None) == sq.SQ_EINVAL
+    L = C.c_double()
+    assert lib.sq_cnn_forward(None, 4, 4, 4, None, None) == sq.SQ_EINVAL
+    assert lib.sq_cnn_backward(None, 4, 4, 4, None, None, None, 0, C.byref(L)) == sq.SQ_EINVAL
+    assert lib.sq_cnn_adam_step(None, 1e-3, 0.9, 0.999, 1e-8, 1.0) == sq.SQ_EINVAL
+    assert lib.sq_cnn_set_params(None, None, 0.0, 1.0, 1.0) == sq.SQ_EINVAL
+    lib.sq_cnn_destroy(None)
 
 
 def test_package_fails_loudly_without_library(tmp_path):

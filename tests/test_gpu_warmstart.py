@@ -1,0 +1,65 @@
+"""The learned warm start end to end on a small system: SCF iterations of
+the SQ path supply (V_in, rho) training pairs, the network trains on them
+with its own kernels, and the surrogate SCF (the network in place of the SQ
+solve) gives a starting potential from which the real SCF converges.  The
+parity of the network's kernels is in tests/test_gpu_cnn.py."""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1708_07913_gb300 import SQ_FP64, SQCNN, SQSCF, SQSolver, build, warm_start_potential  # noqa: E402
+
+build()
+DEV = "cuda:0"
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64).ravel()).to(DEV)
+
+
+def test_train_then_warm_start(tmp_path):
+    wl = synth.custom_workload("ws8", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1750)
+    s = synth.make_system(wl)
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    V_loc = _dev(s.V)
+    shape = (wl.n,) * 3
+    pairs = []
+    scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT)
+    plain = scf.run(tol=1e-6, max_iter=60, on_step=lambda V, rho: pairs.append((shape, V.clone(), rho.clone())))
+    assert plain["converged"] and len(pairs) == plain["iterations"]
+    rho_plain = plain["rho"].cpu().numpy().copy()
+
+    net = SQCNN(bf16=True, seed=3, v_shift=float(s.V.mean()), v_scale=float(s.V.std()),
+                rho_scale=float(pairs[-1][2].mean().item()))
+    first = net.train_step(pairs[:3], lr=3e-3)
+    rng = np.random.default_rng(0)
+    for _ in range(60):
+        idx = rng.choice(len(pairs), size=min(3, len(pairs)), replace=False)
+        last = net.train_step([pairs[i] for i in idx], lr=3e-3)
+    assert np.isfinite(last) and last < 0.5 * first
+
+    path = str(tmp_path / "net.npz")
+    net.save(path)
+    again = SQCNN.load(path, device=DEV)
+    assert np.array_equal(again.params(), net.params())
+    r1, r2 = net.predict(shape, V_loc), again.predict(shape, V_loc)
+    assert torch.equal(r1, r2)
+    again.close()
+
+    V0, res = warm_start_potential(net, solver, V_loc, iters=20)
+    assert len(res) >= 1 and np.all(np.isfinite(res))
+    warm = scf.run(V0=V0, tol=1e-6, max_iter=60)
+    assert warm["converged"]
+    np.testing.assert_allclose(warm["rho"].cpu().numpy(), rho_plain, atol=1e-5 * np.abs(rho_plain).max())
+    print(f"SCF iterations: plain {plain['iterations']}, warm start {warm['iterations']}")
+    net.close()
+    scf.close()
+    solver.close()
