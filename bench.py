@@ -12,6 +12,10 @@ projectors, 324 electrons; synthetic, seeded inputs.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
                   [--impl reference]
+  python bench.py --workload batch16          (16 uneven systems as one CUDA graph)
+  python bench.py --workload force_al108_48   (nonlocal atomic forces, FP64)
+  python bench.py --workload warmstart_c4     (train the warm-start network, then SCF
+                                               iterations to 1e-6 on al256_64 with and without it)
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 on its own GPU (the path has no data exchange between replicas); the JSON line
@@ -56,6 +60,10 @@ def parse():
     p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     p.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (nodes); 0 = automatic")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--train-geometries", type=int, default=250, help="warmstart_c4: seeded training geometries")
+    p.add_argument("--train-iters", type=int, default=8, help="warmstart_c4: SCF iterations kept per geometry")
+    p.add_argument("--train-steps", type=int, default=1000, help="warmstart_c4: Adam steps")
+    p.add_argument("--max-scf", type=int, default=60, help="warmstart_c4: SCF iteration limit")
     return p.parse_args()
 
 
@@ -493,6 +501,182 @@ def run_batch(a):
     print(json.dumps(line), flush=True)
 
 
+FORCE_METRIC = "force node-steps/s (nodes inside a projector support x n_pl per second, one force evaluation)"
+FORCE_UNIT = "node-steps/s"
+FORCE_FLOPS_PER_POINT = 50   # per region point per step: stencil, diagonal, shift/scale, three-term update, D update
+
+
+def touched_nodes(wl, positions):
+    """Nodes inside some projector support (|x - R - image| < r_nl): the
+    nodes the force visits."""
+    n, h, rnl = wl.n, wl.h, synth.PROJ_RNL
+    mark = np.zeros((n, n, n), dtype=bool)
+    for R in positions:
+        lo = [int(math.ceil((R[d] - rnl) / h)) for d in range(3)]
+        hi = [int(math.floor((R[d] + rnl) / h)) for d in range(3)]
+        g = [np.arange(lo[d], hi[d] + 1) for d in range(3)]
+        dx = [g[d] * h - R[d] for d in range(3)]
+        inside = (dx[2][:, None, None] ** 2 + dx[1][None, :, None] ** 2 + dx[0][None, None, :] ** 2) < rnl * rnl
+        iz, iy, ix = np.nonzero(inside)
+        mark[np.mod(g[2][iz], n), np.mod(g[1][iy], n), np.mod(g[0][ix], n)] = True
+    return int(mark.sum())
+
+
+def _oracle_force_chunk(nodes):
+    wl, osys = _W["wl"], _W["osys"]
+    chi, zeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
+    t0 = time.perf_counter()
+    osys.nl_force(nodes, chi, zeta, wl.npl, float(np.median(chi)), wl.kT)
+    return time.perf_counter() - t0
+
+
+def run_force(a):
+    """Nonlocal atomic forces (sq_nl_forces, FP64) on the workload named
+    after ``force_``, with the spectral bounds and Fermi level of one SQ
+    step computed first (not timed).  One step = one force evaluation."""
+    import torch
+    from paper_1708_07913_gb300 import SQ_FP64, SQSolver, build
+
+    name = a.workload[len("force_"):]
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    build()
+    s = synth.make_system(name)
+    wl = s.wl
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=str(dev))
+    Vh = torch.from_numpy(s.V.ravel().copy()).pin_memory()
+    V = Vh.to(dev)
+    out = solver.solve(V, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)
+    mu = out["mu"]
+    chi_h, zeta_h = solver.chi.cpu().pin_memory(), solver.zeta.cpu().pin_memory()
+    F_h = torch.empty(wl.n_atoms * 3, dtype=torch.float64).pin_memory()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    for _ in range(a.warmup):
+        solver.nl_forces(V, mu, wl.kT)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = solver.launches
+    times = []
+    for _ in range(a.steps):
+        flush.fill_(1.0)
+        e0, e1 = ev(), ev()
+        e0.record(stream)
+        F = solver.nl_forces(V, mu, wl.kT)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    launches = solver.launches - launches0
+    e2e = []
+    for _ in range(max(2, a.steps // 2)):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        V.copy_(Vh, non_blocking=True)
+        solver.chi.copy_(chi_h, non_blocking=True)
+        solver.zeta.copy_(zeta_h, non_blocking=True)
+        F = solver.nl_forces(V, mu, wl.kT)
+        F_h.copy_(F.reshape(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        e2e.append(time.perf_counter() - t0)
+    clk = clocks.stop()
+    t = float(np.mean(times))
+    nt = touched_nodes(wl, s.positions)
+    S = 2 * wl.m + 1
+    units = nt * wl.npl
+    flops = nt * wl.npl * S ** 3 * (FORCE_FLOPS_PER_POINT + NL_FLOPS_PER_PAIR * nl_pairs_per_point(wl))
+    peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = 1.25 * sms / SM_COUNT_GB300 * sm_max / 2070.0
+    line = {
+        "metric": FORCE_METRIC, "value": units / t, "unit": FORCE_UNIT, "n_gpus": 1, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded FCC Al-like crystal, Gaussian V and KB projectors)",
+        "config": {"workload": f"{a.workload}: nonlocal forces on {name} ({wl.n_atoms} atoms, {wl.n}^3 grid, "
+                               f"{S}^3 regions, n_pl={wl.npl}, kT={wl.kT}); {nt} of {wl.n_nodes} nodes inside "
+                               f"a projector support",
+                   "precision": "FP64 throughout", "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "single GPU"},
+        "forces_max_abs": float(F.abs().max().item()),
+        "roofline": {"kernel": "nl_force_kernel", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+                     "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
+                     "peak_basis": f"FP64 at GB300's published 1.25 TFLOP/s scaled to {sm_max:.0f} MHz x {sms} SMs"},
+        "e2e": {"value": units / float(np.median(e2e)), "unit": FORCE_UNIT,
+                "h2d_bytes_per_step": 3 * wl.n_nodes * 8, "d2h_bytes_per_step": wl.n_atoms * 3 * 8},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not a.no_cpu_baseline:
+        cores = os.cpu_count() or 1
+        sample = a.cpu_sample or cores * 8
+        try:
+            pool = OraclePool(name, cores)
+            nodes = synth.sample_nodes(wl.n_nodes, sample, seed=4321)
+            chunks = [c for c in np.array_split(nodes, cores) if len(c)]
+            tc = max(pool.pool.map(_oracle_force_chunk, chunks))
+            pool.close()
+            line["cpu_baseline"] = {"value": len(nodes) * wl.npl / tc, "unit": FORCE_UNIT, "cores": len(chunks),
+                                    "kind": "oracle",
+                                    "sample": f"{len(nodes)} seeded nodes of {name} (or_nl_force after the "
+                                              f"oracle's own bounds; force part timed), per-node rate"}
+        except Exception as exc:
+            line["cpu_baseline"] = {"value": None, "unit": FORCE_UNIT, "cores": 0, "kind": "oracle",
+                                    "sample": f"failed: {exc}"}
+    solver.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_warmstart(a):
+    """The learned warm start on the 4x4x4-cell system (al256_64): training
+    pairs from SCF iterations of seeded one-cell geometries with the same
+    grid spacing, region, degree and temperature; training of the network
+    with its own kernels; then the SCF of al256_64 to 1e-6 from V_loc and
+    from the warm start.  Value: SCF iterations with the warm start."""
+    import torch
+    from paper_1708_07913_gb300 import SQCNN, build
+    from paper_1708_07913_gb300 import warmstart as wsm
+
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    build()
+    target = synth.WORKLOADS["al256_64"]
+    tmpl = synth.custom_workload("ws_train", cells=1, n=16, r_cut=target.r_cut, npl=target.npl, kT=target.kT,
+                                 sigma_disp=target.sigma_disp, nonlocal_=True, seed=0)
+    clocks = ClockSampler(0)
+    clocks.start()
+    pairs, t_data = wsm.training_pairs(tmpl, a.train_geometries, a.train_iters, seed=5000, device=str(dev))
+    net = SQCNN(True, 0, *wsm.input_scales(pairs), device=str(dev))
+    losses, t_train = wsm.train(net, pairs, a.train_steps)
+    res = wsm.compare(net, target, tol=1e-6, max_iter=a.max_scf, device=str(dev))
+    clk = clocks.stop()
+    net.close()
+    line = {
+        "metric": "SCF iterations to a 1e-6 residual (al256_64) with the learned warm start",
+        "value": res["warm_iterations"], "unit": "iterations", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": res["warm_s"] * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16 network (FP32 accumulation), FP32 SQ recurrence with FP64 moments",
+        "data": "synthetic (seeded FCC Al-like crystals, Gaussian V and KB projectors)",
+        "config": {"workload": "warmstart_c4: target al256_64 (4^3 cells, 256 atoms, 64^3 grid, 25^3 regions, "
+                               "n_pl=48, kT=0.05); training on one-cell 16^3 geometries",
+                   "training_pairs": len(pairs), "training_geometries": a.train_geometries,
+                   "scf_iterations_per_geometry": a.train_iters, "adam_steps": a.train_steps,
+                   "parallelism": "single GPU"},
+        "plain_iterations": res["plain_iterations"], "plain_converged": res["plain_converged"],
+        "warm_converged": res["warm_converged"], "plain_residuals": res["plain_residuals"],
+        "warm_residuals": res["warm_residuals"], "surrogate_steps": res["surrogate_steps"],
+        "surrogate_residual": res["surrogate_residual"], "rho_rel_diff_plain_vs_warm": res["rho_rel_diff"],
+        "seconds": {"training_data": t_data, "training": t_train, "surrogate": res["surrogate_s"],
+                    "scf_plain": res["plain_s"], "scf_warm": res["warm_s"]},
+        "loss_first_last": [losses[0], losses[-1]],
+        "roofline": None, "e2e": None, "cpu_baseline": None, "gpu_launches": None, "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     a = parse()
     if a.warmup < 3:
@@ -501,6 +685,10 @@ def main():
         run_reference(a)
     elif a.workload == "batch16":
         run_batch(a)
+    elif a.workload.startswith("force_"):
+        run_force(a)
+    elif a.workload == "warmstart_c4":
+        run_warmstart(a)
     else:
         run_gb300(a)
 

@@ -1,0 +1,98 @@
+"""The learned SCF warm start on a workload, end to end:
+
+1. training pairs: for seeded geometries of a small training cell, SCF
+   iterations of the SQ path, keeping every (V_in, rho = SQ(V_in)) pair;
+2. training: Adam on random minibatches of those pairs (SQCNN.train_step);
+3. comparison: the SCF of the target system from V_loc and from the
+   network's starting potential (warm_start_potential), iterations counted
+   to the same residual.
+
+Every step runs in libsq (the SQ path, Poisson, effective potential, mixer
+and the network's kernels); this module sequences calls and keeps the pairs
+on the device.
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+import synth
+
+from . import SQ_FP32, SQCNN, SQSCF, SQSolver, warm_start_potential
+
+
+def training_pairs(template, n_geometries, iters, seed, precision=SQ_FP32, device="cuda:0"):
+    """(shape, V_in, rho) device pairs from ``iters`` SCF iterations on each
+    of ``n_geometries`` geometries of ``template`` (a synth.Workload), seeds
+    seed, seed + 1, ...  Returns (pairs, seconds)."""
+    import torch
+    pairs = []
+    t0 = time.perf_counter()
+    for g in range(n_geometries):
+        wl = dataclasses.replace(template, name=f"{template.name}-g{g}", seed=seed + g)
+        s = synth.make_system(wl)
+        solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=device)
+        V_loc = torch.from_numpy(s.V.ravel().copy()).to(device)
+        scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, margin=wl.margin)
+        shape = (wl.n,) * 3
+        scf.run(tol=0.0, max_iter=iters, on_step=lambda V, rho: pairs.append((shape, V.clone(), rho.clone())))
+        scf.close()
+        solver.close()
+    torch.cuda.synchronize()
+    return pairs, time.perf_counter() - t0
+
+
+def input_scales(pairs):
+    """(v_shift, v_scale, rho_scale) from the training pairs: mean and
+    standard deviation of V, mean of rho (host reductions of copies)."""
+    V = np.concatenate([p[1].cpu().numpy() for p in pairs[: min(len(pairs), 64)]])
+    rho = np.concatenate([p[2].cpu().numpy() for p in pairs[: min(len(pairs), 64)]])
+    return float(V.mean()), float(V.std()), float(rho.mean())
+
+
+def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=0):
+    """Adam on random minibatches, learning rate decayed geometrically from
+    lr to lr_final.  Returns (losses, seconds)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    losses = []
+    t0 = time.perf_counter()
+    for k in range(steps):
+        r = lr * (lr_final / lr) ** (k / max(1, steps - 1))
+        idx = rng.choice(len(pairs), size=min(batch, len(pairs)), replace=False)
+        losses.append(net.train_step([pairs[i] for i in idx], r))
+        if log_every and k % log_every == 0:
+            print(f"step {k} loss {losses[-1]:.4e}", flush=True)
+    torch.cuda.synchronize()
+    return losses, time.perf_counter() - t0
+
+
+def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=7):
+    """SCF iterations of ``wl`` from V_loc and from the warm start."""
+    import torch
+    s = synth.make_system(wl)
+    solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=device)
+    V_loc = torch.from_numpy(s.V.ravel().copy()).to(device)
+    scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=beta, history=history, margin=wl.margin)
+    t0 = time.perf_counter()
+    plain = scf.run(tol=tol, max_iter=max_iter)
+    t_plain = time.perf_counter() - t0
+    rho_plain = plain["rho"].clone()
+    t0 = time.perf_counter()
+    V0, surrogate = warm_start_potential(net, solver, V_loc)
+    t_surr = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    warm = scf.run(V0=V0, tol=tol, max_iter=max_iter)
+    t_warm = time.perf_counter() - t0
+    drho = float((warm["rho"] - rho_plain).abs().max().item() / rho_plain.abs().max().item())
+    out = dict(plain_iterations=plain["iterations"], plain_converged=plain["converged"],
+               plain_residuals=[float(r) for r in plain["residuals"]], plain_s=t_plain,
+               warm_iterations=warm["iterations"], warm_converged=warm["converged"],
+               warm_residuals=[float(r) for r in warm["residuals"]], warm_s=t_warm,
+               surrogate_steps=len(surrogate), surrogate_residual=float(surrogate[-1]), surrogate_s=t_surr,
+               rho_rel_diff=drho)
+    scf.close()
+    solver.close()
+    return out

@@ -83,6 +83,10 @@ WORKLOADS = {
                          sigma_disp=0.15, nonlocal_=True, seed=1709),
     "al2048_128": Workload("al2048_128", cells=8, n=128, r_cut=7.0, npl=64, kT=0.1,
                            sigma_disp=0.2, nonlocal_=True, seed=1712),
+    # the learned-warm-start SCF target: 4x4x4 cells (256 atoms), 64^3 grid,
+    # with the region, degree and temperature of al108_48
+    "al256_64": Workload("al256_64", cells=4, n=64, r_cut=6.0, npl=48, kT=0.05,
+                         sigma_disp=0.15, nonlocal_=True, seed=1711),
     # profiling case: same region size, degree and projectors as al108_48 on a
     # 2x2x2-cell (32^3) grid, so the same kernels run on 30% of the nodes
     "al32_32": Workload("al32_32", cells=2, n=32, r_cut=6.0, npl=48, kT=0.05,

@@ -120,6 +120,11 @@ def test_cnn_host_checks(lib):
     lib.sq_cnn_destroy(None)
 
 
+def test_warm_start_driver_imports():
+    from paper_1708_07913_gb300 import warmstart
+    assert callable(warmstart.training_pairs) and callable(warmstart.compare)
+
+
 def test_package_fails_loudly_without_library(tmp_path):
     from paper_1708_07913_gb300 import sq
     with pytest.raises(RuntimeError):
