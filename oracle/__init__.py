@@ -78,6 +78,8 @@ def _load():
             lib.or_xalpha.argtypes = [C.c_long, dp, C.c_double, dp]
             lib.or_xalpha.restype = None
             lib.or_anderson_step.argtypes = [C.c_long, C.c_int, dp, dp, C.c_double, dp]
+            lib.or_kerker.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, C.c_double, C.c_double, dp, dp,
+                                      C.c_double, C.c_int, ip]
             _lib = lib
     return _lib
 
@@ -294,15 +296,35 @@ def anderson_step(Xs, Fs, beta):
     return out
 
 
+def kerker(f, h, k0, amin, no=6, tol=1e-12, max_iter=5000):
+    """(-lap_h + amin k0^2)(-lap_h + k0^2)^{-1} f on the periodic grid; f has
+    shape (n3, n2, n1).  Returns (y, CG iterations)."""
+    f = _f64(f)
+    y = np.zeros_like(f)
+    n3, n2, n1 = f.shape
+    it = C.c_int()
+    rc = _load().or_kerker(n1, n2, n3, float(h), int(no), float(k0), float(amin), _dp(f), _dp(y), float(tol),
+                           int(max_iter), C.byref(it))
+    if rc == 1:
+        raise ValueError("bad arguments")
+    return y, it.value
+
+
+_kerker = kerker      # the scf() argument of the same name shadows it there
+
+
 def scf(V_loc, h, m, positions, proj_types, n_electrons, kT, npl, alpha=2.0 / 3.0, beta=0.3, history=7,
-        tol=1e-6, max_iter=60, n_lanczos=40, margin=0.01, periodic=False, fd_half_order=6, poisson_tol=1e-12):
+        tol=1e-6, max_iter=60, n_lanczos=40, margin=0.01, periodic=False, fd_half_order=6, poisson_tol=1e-12,
+        kerker=None):
     """The SCF loop of Section 3 around the SQ path, with the effective
     potential as the fixed-point variable: V_in -> SQ density rho[V_in] ->
     V_out = V_loc + phi[rho] + v_x[rho] (phi: Eq. PoissonEqn with a
     neutralising background; v_x: Slater X-alpha), stopped when
     ||V_out - V_in|| <= tol ||V_out|| (2-norms); Anderson mixing with the last
-    `history` differences.  Starts from V_in = V_loc.  Returns a dict with the
-    converged V_in, rho, mu, energies, the residual history and iterations."""
+    `history` differences.  Starts from V_in = V_loc.  ``kerker`` = (k0, amin)
+    mixes the preconditioned residual P f (or_kerker) in place of f; the
+    stopping test stays on f.  Returns a dict with the converged V_in, rho,
+    mu, energies, the residual history and iterations."""
     V_loc = _f64(V_loc)
     V_in = V_loc.copy()
     Xs, Fs, res = [], [], []
@@ -318,6 +340,8 @@ def scf(V_loc, h, m, positions, proj_types, n_electrons, kT, npl, alpha=2.0 / 3.
         if res[-1] <= tol:
             return dict(V=V_in, V_out=V_out, rho=rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
                         n_elec=out["n_elec"], residuals=res, iterations=it + 1, converged=True)
+        if kerker is not None:
+            f = _kerker(f.reshape(V_loc.shape), h, kerker[0], kerker[1], fd_half_order)[0].ravel()
         Xs.append(V_in.ravel().copy())
         Fs.append(f.copy())
         Xs, Fs = Xs[-(history + 1):], Fs[-(history + 1):]

@@ -11,11 +11,13 @@
  * check and the benchmark's CPU leg are the only callers; it shares no code
  * with the CUDA library.
  *
- * Parity status: or_laplacian_periodic, or_poisson_cg, or_xalpha and
- * or_anderson_step are pinned by tests/test_oracle_scf.py (discrete Fourier
- * symbol of the operator, exact spectral solve, derivative of the exchange
- * energy, finite termination of Anderson mixing on linear maps); the SCF
- * loop built from them is pinned against dense diagonalisation.
+ * Parity status: or_laplacian_periodic, or_poisson_cg, or_xalpha,
+ * or_anderson_step and or_kerker are pinned by tests/test_oracle_scf.py
+ * (discrete Fourier symbol of the operator, exact spectral solve, derivative
+ * of the exchange energy, finite termination of Anderson mixing on linear
+ * maps, the preconditioner's Fourier symbol); the SCF loop built from them
+ * is pinned against dense diagonalisation, with and without the
+ * preconditioner.
  */
 #include <math.h>
 #include <stdlib.h>
@@ -194,4 +196,47 @@ int or_anderson_step(long n, int mh, const double *Xs, const double *Fs, double 
         x_next[t] = v;
     }
     return dropped;
+}
+
+/* Kerker-type preconditioner of an SCF residual f (a reading: the paper's
+ * Periodic Pulay mixing is used with such a preconditioner in its SPARC
+ * lineage, but the paper does not state one):
+ *   y = (-lap_h + a k0^2) (-lap_h + k0^2)^{-1} f = f - (1 - a) k0^2 u,
+ *   (-lap_h + k0^2) u = f,
+ * i.e. the Fourier symbol (S + a k0^2)/(S + k0^2) with S >= 0 the symbol of
+ * -lap_h: wavelengths long against 2 pi/k0 are scaled by a (0 < a <= 1; the
+ * mean by exactly a), short ones pass.  u by conjugate gradients from 0
+ * until ||f - A u|| <= tol ||f|| or max_iter iterations.  Returns 0, 1 on
+ * bad arguments, 2 if max_iter was reached. */
+int or_kerker(int n1, int n2, int n3, double h, int no, double k0, double amin, const double *f, double *y,
+              double tol, int max_iter, int *iters)
+{
+    if (!(k0 > 0.0) || !(amin > 0.0) || !(amin <= 1.0)) return 1;
+    const long n = (long)n1 * n2 * n3;
+    const double s = k0 * k0;
+    double *u = calloc(n, sizeof(double)), *r = malloc(sizeof(double) * n);
+    double *p = malloc(sizeof(double) * n), *Ap = malloc(sizeof(double) * n);
+    if (!u || !r || !p || !Ap) { free(u); free(r); free(p); free(Ap); return 1; }
+    for (long i = 0; i < n; ++i) { r[i] = f[i]; p[i] = f[i]; }
+    const double fnorm = sqrt(dot(n, f, f));
+    double rr = dot(n, r, r);
+    int it = 0, status = 0;
+    while (fnorm > 0.0 && sqrt(rr) > tol * fnorm) {
+        if (it >= max_iter) { status = 2; break; }
+        or_laplacian_periodic(n1, n2, n3, h, no, p, Ap);
+        for (long i = 0; i < n; ++i) Ap[i] += s * p[i];
+        const double alpha = rr / dot(n, p, Ap);
+        for (long i = 0; i < n; ++i) {
+            u[i] += alpha * p[i];
+            r[i] -= alpha * Ap[i];
+        }
+        const double rr_new = dot(n, r, r);
+        for (long i = 0; i < n; ++i) p[i] = r[i] + (rr_new / rr) * p[i];
+        rr = rr_new;
+        ++it;
+    }
+    for (long i = 0; i < n; ++i) y[i] = f[i] - (1.0 - amin) * s * u[i];
+    if (iters) *iters = it;
+    free(u); free(r); free(p); free(Ap);
+    return status;
 }

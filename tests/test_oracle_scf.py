@@ -64,6 +64,21 @@ def test_poisson_is_the_exact_discrete_solve():
     assert np.abs(zero).max() < 1e-14
 
 
+def test_kerker_is_its_fourier_symbol():
+    """(-lap_h + a k0^2)(-lap_h + k0^2)^-1 is the multiplier (S + a k0^2)/(S + k0^2)
+    in Fourier space; the mean is scaled by exactly a."""
+    rng = np.random.default_rng(11)
+    n, h = 9, 0.6
+    f = rng.standard_normal((n, n, n)) + 0.4
+    for k0, a in ((1.0, 0.1), (0.5, 1.0), (2.0, 0.3)):
+        y, it = oracle.kerker(f, h, k0, a, tol=1e-13)
+        S = _symbol(n, h)
+        ref = np.real(np.fft.ifftn(np.fft.fftn(f) * (S + a * k0 ** 2) / (S + k0 ** 2)))
+        np.testing.assert_allclose(y, ref, atol=1e-11 * np.abs(f).max())
+        assert abs(y.mean() - a * f.mean()) < 1e-12 and 0 < it < n ** 3
+    np.testing.assert_allclose(oracle.kerker(f, h, 1.0, 1.0)[0], f, atol=1e-11)      # a = 1: identity
+
+
 def test_xalpha_is_the_derivative_of_the_exchange_energy():
     """v_x = d e_x / d rho with e_x = -(9 alpha/8)(3/pi)^(1/3) rho^(4/3);
     alpha = 2/3 gives the uniform-gas exchange -(3 rho/pi)^(1/3)."""
@@ -140,10 +155,11 @@ def test_scf_reaches_the_dense_diagonalisation_fixed_point():
     V_loc = synth.local_potential(n, L, pos)
     Ne, kT = 12.0, 0.5
     V_ref, rho_ref, mu_ref = _dense_scf(V_loc, h, Ne, kT)
-    r = oracle.scf(V_loc, h, 0, pos, (), Ne, kT, npl=100, tol=1e-8, periodic=True, n_lanczos=60)
-    assert r["converged"] and r["iterations"] < 40
-    assert r["residuals"][-1] <= 1e-8 < r["residuals"][0]
-    np.testing.assert_allclose(r["V"], V_ref, atol=1e-6 * np.abs(V_ref).max())
-    np.testing.assert_allclose(r["rho"], rho_ref, atol=1e-6 * rho_ref.max())
-    assert abs(r["mu"] - mu_ref) < 1e-6
-    assert abs(r["n_elec"] - Ne) < 1e-9 * Ne
+    for kerker in (None, (1.0, 0.2)):           # the fixed point does not depend on the preconditioner
+        r = oracle.scf(V_loc, h, 0, pos, (), Ne, kT, npl=100, tol=1e-8, periodic=True, n_lanczos=60, kerker=kerker)
+        assert r["converged"] and r["iterations"] < 40
+        assert r["residuals"][-1] <= 1e-8 < r["residuals"][0]
+        np.testing.assert_allclose(r["V"], V_ref, atol=1e-6 * np.abs(V_ref).max())
+        np.testing.assert_allclose(r["rho"], rho_ref, atol=1e-6 * rho_ref.max())
+        assert abs(r["mu"] - mu_ref) < 1e-6
+        assert abs(r["n_elec"] - Ne) < 1e-9 * Ne
