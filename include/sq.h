@@ -265,6 +265,20 @@ void sq_batch_destroy(sq_batch *b);
  *   V_out = V_loc + phi + v_x(rho), v_x = -(3 alpha / 2)(3 rho / pi)^(1/3)
  *   (Slater X-alpha; alpha = 2/3 is uniform-gas exchange; 0 where rho <= 0).
  *   All device, N_d FP64; 0 < alpha < 10.  Asynchronous.
+ * sq_kerker(ctx, v_in, v_out, k0, amin, tol, max_iter, v_pre, rel_resid_host,
+ *           iters_host)
+ *   Preconditioned SCF residual for the mixer: with f = v_out - v_in,
+ *   v_pre = v_in + P f,  P = (-lap_h + amin k0^2)(-lap_h + k0^2)^{-1}
+ *   (Kerker-type; Fourier symbol (S + amin k0^2)/(S + k0^2), S the symbol
+ *   of -lap_h: long wavelengths scaled by amin, the mean exactly, short
+ *   ones passed).  (-lap_h + k0^2) u = f by conjugate gradients from 0
+ *   until ||f - A u|| <= tol ||f||, then v_pre = v_in + f - (1 - amin) k0^2 u.
+ *   Giving (v_in, v_pre) to sq_mixer_step mixes P f in place of f.
+ *   rel_resid_host (HOST, may be NULL) = ||f|| / ||v_out||, the
+ *   unpreconditioned residual; iters_host (may be NULL) the CG iterations.
+ *   All device, N_d FP64; v_pre must not alias v_in or v_out; k0 > 0,
+ *   0 < amin <= 1, 0 < tol < 1, max_iter >= 0.  Uses the context's Poisson
+ *   workspace.  SQ_ENOCONV if max_iter is reached.  Synchronises the stream.
  * sq_mixer_create(out, n, history, beta, cuda_stream)
  *   An Anderson mixer for vectors of n doubles keeping the last `history`
  *   (0..16) differences, mixing parameter 0 < beta <= 1, on cuda_stream
@@ -287,6 +301,8 @@ int sq_poisson(sq_ctx *ctx, const double *rho, double *phi, double tol, int max_
                int *iters_host, double *rel_resid_host);
 int sq_effective_potential(sq_ctx *ctx, const double *V_loc, const double *phi, const double *rho,
                            double alpha, double *V_out);
+int sq_kerker(sq_ctx *ctx, const double *v_in, const double *v_out, double k0, double amin, double tol,
+              int max_iter, double *v_pre, double *rel_resid_host, int *iters_host);
 typedef struct sq_mixer sq_mixer;
 int sq_mixer_create(sq_mixer **out, long long n, int history, double beta, void *cuda_stream);
 int sq_mixer_step(sq_mixer *mx, const double *v_in, const double *v_out, double *v_next,

@@ -154,14 +154,19 @@ class SQSCF:
     sequences them."""
 
     def __init__(self, solver, V_loc, n_electrons, kT, alpha=2.0 / 3.0, beta=0.3, history=7, n_lanczos=40,
-                 margin=0.01):
+                 margin=0.01, kerker=None):
+        """``kerker`` = (k0, amin): mix the Kerker-preconditioned residual
+        (sq_kerker) in place of V_out - V_in; the stopping test stays on the
+        unpreconditioned residual."""
         torch = solver.torch
         self.solver, self.V_loc = solver, V_loc
+        self.kerker = None if kerker is None else (float(kerker[0]), float(kerker[1]))
         self.n_electrons, self.kT, self.alpha = float(n_electrons), float(kT), float(alpha)
         self.n_lanczos, self.margin = int(n_lanczos), float(margin)
         f64 = dict(dtype=torch.float64, device=solver.device)
         self.phi = torch.empty(solver.n_nodes, **f64)
         self.V_out = torch.empty(solver.n_nodes, **f64)
+        self.V_pre = torch.empty(solver.n_nodes, **f64) if kerker is not None else None
         self._V = [torch.empty(solver.n_nodes, **f64), torch.empty(solver.n_nodes, **f64)]
         with torch.cuda.device(solver.device):
             self.mixer = sq.sq_mixer_create(solver.n_nodes, history, beta)
@@ -195,7 +200,12 @@ class SQSCF:
             k, _ = sq.sq_poisson(sv.ctx, sv.rho, self.phi, poisson_tol)
             pit.append(k)
             sq.sq_effective_potential(sv.ctx, self.V_loc, self.phi, sv.rho, self.alpha, self.V_out)
-            res.append(sq.sq_mixer_step(self.mixer, V_in, self.V_out, V_next))
+            if self.kerker is None:
+                res.append(sq.sq_mixer_step(self.mixer, V_in, self.V_out, V_next))
+            else:
+                r, _ = sq.sq_kerker(sv.ctx, V_in, self.V_out, self.kerker[0], self.kerker[1], self.V_pre)
+                sq.sq_mixer_step(self.mixer, V_in, self.V_pre, V_next)
+                res.append(r)
             if res[-1] <= tol:
                 return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
                             n_elec=out["n_elec"], residuals=res, iterations=it + 1, converged=True,

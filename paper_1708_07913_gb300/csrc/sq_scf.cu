@@ -153,6 +153,36 @@ __global__ void sub_kernel(const double* __restrict__ a, const double* __restric
         out[t] = a[t] - b[t];
 }
 
+// y = -lap_h x + s x on the periodic grid (the operator of the preconditioner)
+__global__ void helmholtz_kernel(const double* __restrict__ x, double* __restrict__ y, int n1, int n2, int n3,
+                                 FDW fw, double s)
+{
+    const long long n = (long long)n1 * n2 * n3;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n; p += (long long)gridDim.x * blockDim.x) {
+        const int i = (int)(p % n1), j = (int)((p / n1) % n2), k = (int)(p / ((long long)n1 * n2));
+        const long long row = p - i, plane = p - i - (long long)j * n1;
+        double acc = 6.0 * fw.w[0] * x[p];
+        for (int d = 1; d <= FD_NO; ++d) {
+            const int ip = (i + d) % n1, im = ((i - d) % n1 + n1) % n1;
+            const int jp = (j + d) % n2, jm = ((j - d) % n2 + n2) % n2;
+            const int kp = (k + d) % n3, km = ((k - d) % n3 + n3) % n3;
+            const double sx = x[row + ip] + x[row + im];
+            const double sy = x[plane + (long long)jp * n1 + i] + x[plane + (long long)jm * n1 + i];
+            const double sz = x[((long long)kp * n2 + j) * n1 + i] + x[((long long)km * n2 + j) * n1 + i];
+            acc += fw.w[d] * ((sx + sy) + sz);
+        }
+        y[p] = s * x[p] - acc;
+    }
+}
+
+// out = v_in + f - c u (u is read from out)
+__global__ void kerker_out_kernel(const double* __restrict__ v_in, const double* __restrict__ f, double c,
+                                  double* __restrict__ out, long long n)
+{
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        out[t] = v_in[t] + f[t] - c * out[t];
+}
+
 // Reduction scratch: partials, a counter and a few result slots.
 struct Red {
     double* partials = nullptr;
@@ -247,6 +277,35 @@ void ws_free(PoissonWS* w)
     red_free(w->red);
     delete w;
 }
+
+// The context's workspace of 4 N doubles and a reduction (created on first
+// use; shared by the Poisson solve and the preconditioner).
+int context_ws(sq_ctx* c, PoissonWS** out)
+{
+    const long long n = c->g.Nd;
+    PoissonWS* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_ws_mutex);
+        auto it = g_ws.find(c);
+        if (it != g_ws.end()) ws = it->second;
+    }
+    if (!ws) {
+        ws = new (std::nothrow) PoissonWS();
+        if (!ws) return SQ_ENOMEM;
+        int rc = cudaMalloc(&ws->buf, sizeof(double) * 4 * n) == cudaSuccess ? SQ_OK : SQ_ENOMEM;
+        if (rc == SQ_OK) rc = red_alloc(ws->red, c->sm_count, 8);
+        if (rc) {
+            cudaGetLastError();
+            ws_free(ws);
+            return rc;
+        }
+        ws->n = n;
+        std::lock_guard<std::mutex> lk(g_ws_mutex);
+        g_ws[c] = ws;
+    }
+    *out = ws;
+    return SQ_OK;
+}
 }  // namespace
 
 namespace sq {
@@ -321,25 +380,8 @@ int sq_poisson(sq_ctx* c, const double* rho, double* phi, double tol, int max_it
     const long long n = c->g.Nd;
     cudaStream_t st = c->stream;
     PoissonWS* ws = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_ws_mutex);
-        auto it = g_ws.find(c);
-        if (it != g_ws.end()) ws = it->second;
-    }
-    if (!ws) {
-        ws = new (std::nothrow) PoissonWS();
-        if (!ws) return SQ_ENOMEM;
-        int rc = cudaMalloc(&ws->buf, sizeof(double) * 4 * n) == cudaSuccess ? SQ_OK : SQ_ENOMEM;
-        if (rc == SQ_OK) rc = red_alloc(ws->red, c->sm_count, 8);
-        if (rc) {
-            cudaGetLastError();
-            ws_free(ws);
-            return rc;
-        }
-        ws->n = n;
-        std::lock_guard<std::mutex> lk(g_ws_mutex);
-        g_ws[c] = ws;
-    }
+    int rcw = context_ws(c, &ws);
+    if (rcw) return rcw;
     Red& R = ws->red;
     double* b = ws->buf;
     double* r = b + n;
@@ -401,6 +443,63 @@ int sq_effective_potential(sq_ctx* c, const double* V_loc, const double* phi, co
     veff_kernel<<<grid_for(n, c->sm_count), 256, 0, c->stream>>>(V_loc, phi, rho, alpha, V_out, n);
     c->launches++;
     return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;
+}
+
+int sq_kerker(sq_ctx* c, const double* v_in, const double* v_out, double k0, double amin, double tol, int max_iter,
+              double* v_pre, double* rel_resid_host, int* iters_host)
+{
+    if (!c || !(k0 > 0.0) || !(amin > 0.0) || !(amin <= 1.0) || !(tol > 0.0) || !(tol < 1.0) || max_iter < 0)
+        return SQ_EINVAL;
+    if (!device_ptr(v_in) || !device_ptr(v_out) || !device_ptr(v_pre) || v_pre == v_in || v_pre == v_out)
+        return SQ_EINVAL;
+    const long long n = c->g.Nd;
+    cudaStream_t st = c->stream;
+    PoissonWS* ws = nullptr;
+    int rc = context_ws(c, &ws);
+    if (rc) return rc;
+    Red& R = ws->red;
+    double* f = ws->buf;
+    double* r = f + n;
+    double* p = r + n;
+    double* Ap = p + n;
+    double* u = v_pre;
+    const int G = grid_for(n, c->sm_count);
+    const double s = k0 * k0;
+    FDW fw;
+    for (int d = 0; d <= FD_NO; ++d) fw.w[d] = c->g.w[d];
+    sub_kernel<<<G, 256, 0, st>>>(v_out, v_in, f, n);
+    if ((rc = enqueue_dot(R, f, nullptr, f, nullptr, n, 0, st)) || (rc = enqueue_dot(R, v_out, nullptr, v_out, nullptr, n, 1, st)))
+        return rc;
+    c->launches += 3;
+    double h2[2];
+    if ((rc = read_slots(R, h2, 2, st))) return rc;
+    const double fnorm = sqrt(h2[0]);
+    if (rel_resid_host) *rel_resid_host = h2[1] > 0.0 ? fnorm / sqrt(h2[1]) : 0.0;
+    if (cudaMemsetAsync(u, 0, sizeof(double) * n, st) != cudaSuccess ||
+        cudaMemcpyAsync(r, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(p, f, sizeof(double) * n, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        return SQ_ECUDA;
+    double rr = h2[0];
+    int it = 0;
+    while (fnorm > 0.0 && sqrt(rr) > tol * fnorm && it < max_iter) {
+        helmholtz_kernel<<<G, 256, 0, st>>>(p, Ap, c->g.n1, c->g.n2, c->g.n3, fw, s);
+        if ((rc = enqueue_dot(R, p, nullptr, Ap, nullptr, n, 4, st))) return rc;
+        double pAp, rr_new;
+        if ((rc = read_slot(R, 4, &pAp, st))) return rc;
+        const double alpha = rr / pAp;
+        cg_update_kernel<<<G, 256, 0, st>>>(u, r, p, Ap, alpha, n);
+        if ((rc = enqueue_dot(R, r, nullptr, r, nullptr, n, 5, st))) return rc;
+        if ((rc = read_slot(R, 5, &rr_new, st))) return rc;
+        xpby_kernel<<<G, 256, 0, st>>>(p, r, rr_new / rr, n);
+        c->launches += 5;
+        rr = rr_new;
+        ++it;
+    }
+    kerker_out_kernel<<<G, 256, 0, st>>>(v_in, f, (1.0 - amin) * s, v_pre, n);
+    c->launches++;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    if (iters_host) *iters_host = it;
+    return (fnorm > 0.0 && sqrt(rr) > tol * fnorm) ? SQ_ENOCONV : SQ_OK;
 }
 
 int sq_mixer_create(sq_mixer** out, long long n, int history, double beta, void* cuda_stream)

@@ -26,7 +26,7 @@ EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
            "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
            "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
-           "sq_nl_forces", "sq_cnn_param_count", "sq_cnn_create", "sq_cnn_set_params", "sq_cnn_get_params",
+           "sq_nl_forces", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create", "sq_cnn_set_params", "sq_cnn_get_params",
            "sq_cnn_forward", "sq_cnn_backward", "sq_cnn_get_grads", "sq_cnn_adam_step", "sq_cnn_destroy")
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         lib.sq_poisson.argtypes = [vp, vp, vp, C.c_double, ip, C.POINTER(ip), dp]
         lib.sq_effective_potential.argtypes = [vp, vp, vp, vp, C.c_double, vp]
         lib.sq_nl_forces.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp]
+        lib.sq_kerker.argtypes = [vp, vp, vp, C.c_double, C.c_double, C.c_double, ip, vp, dp, C.POINTER(ip)]
         lib.sq_cnn_param_count.argtypes = [ip]
         lib.sq_cnn_param_count.restype = C.c_longlong
         lib.sq_cnn_create.argtypes = [C.POINTER(vp), ip, ip, vp]
@@ -265,6 +266,14 @@ def sq_effective_potential(ctx, V_loc, phi, rho, alpha, V_out):
     _check(load().sq_effective_potential(C.c_void_p(ctx), _dptr(V_loc, "V_loc"), _dptr(phi, "phi"),
                                          _dptr(rho, "rho"), float(alpha), _dptr(V_out, "V_out")),
            "sq_effective_potential")
+
+
+def sq_kerker(ctx, v_in, v_out, k0, amin, v_pre, tol=1e-10, max_iter=2000):
+    """Fills v_pre = v_in + P (v_out - v_in); returns (||v_out - v_in|| / ||v_out||, CG iterations)."""
+    res, it = C.c_double(), C.c_int()
+    _check(load().sq_kerker(C.c_void_p(ctx), _dptr(v_in, "v_in"), _dptr(v_out, "v_out"), float(k0), float(amin),
+                            float(tol), int(max_iter), _dptr(v_pre, "v_pre"), C.byref(res), C.byref(it)), "sq_kerker")
+    return res.value, it.value
 
 
 def sq_mixer_create(n, history, beta, stream=None):

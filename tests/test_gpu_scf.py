@@ -127,3 +127,45 @@ def test_scf_checkpoint_and_resume(tmp_path):
     np.testing.assert_allclose(rest["V"].cpu().numpy(), V_full, atol=1e-12 * np.abs(V_full).max())
     scf.close()
     solver.close()
+
+
+def test_kerker_matches_oracle(small):
+    s, solver = small
+    n = s.wl.n
+    rng = np.random.default_rng(12)
+    v_in = rng.standard_normal((n, n, n))
+    v_out = v_in + rng.standard_normal((n, n, n)) * 0.1 + 0.05
+    v_pre = torch.empty(n ** 3, dtype=torch.float64, device=DEV)
+    sq.sq_set_stream(solver.ctx)
+    for k0, amin in ((1.0, 0.2), (0.6, 1.0)):
+        res, it = sq.sq_kerker(solver.ctx, _dev(v_in), _dev(v_out), k0, amin, v_pre, tol=1e-13)
+        y, _ = oracle.kerker(v_out - v_in, s.wl.h, k0, amin, tol=1e-13)
+        ref = v_in + y
+        np.testing.assert_allclose(v_pre.cpu().numpy(), ref.ravel(), atol=1e-10 * np.abs(ref).max())
+        assert abs(res - np.linalg.norm(v_out - v_in) / np.linalg.norm(v_out)) < 1e-13 and it > 0
+    with pytest.raises(sq.SQError) as e:                           # output aliases an input
+        x = _dev(v_in)
+        sq.sq_kerker(solver.ctx, x, _dev(v_out), 1.0, 0.2, x)
+    assert e.value.code == sq.SQ_EINVAL
+
+
+def test_scf_with_kerker_matches_oracle_scf():
+    """The SCF of test_scf_matches_oracle_scf with the Kerker-preconditioned
+    residual mixed: same iterations as the oracle's preconditioned SCF and
+    the same fixed point as without the preconditioner."""
+    wl = synth.custom_workload("scf8k", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1741)
+    s = synth.make_system(wl)
+    pt = synth.projector_types(True)
+    kk = (1.0, 0.2)
+    ref = oracle.scf(s.V, wl.h, wl.m, s.positions, pt, wl.n_electrons, wl.kT, wl.npl, tol=1e-9, max_iter=60,
+                     kerker=kk)
+    assert ref["converged"]
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    scf = SQSCF(solver, _dev(s.V), wl.n_electrons, wl.kT, kerker=kk)
+    out = scf.run(tol=1e-9, max_iter=60)
+    assert out["converged"] and abs(out["iterations"] - ref["iterations"]) <= 1
+    np.testing.assert_allclose(out["residuals"][:5], ref["residuals"][:5], rtol=1e-6)
+    np.testing.assert_allclose(out["V"].cpu().numpy(), ref["V"].ravel(), atol=1e-7 * np.abs(ref["V"]).max())
+    scf.close()
+    solver.close()
