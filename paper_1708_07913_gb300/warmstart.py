@@ -69,13 +69,15 @@ def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=
     return losses, time.perf_counter() - t0
 
 
-def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=7):
-    """SCF iterations of ``wl`` from V_loc and from the warm start."""
+def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=12,
+            kerker=(0.8, 0.2)):
+    """SCF iterations of ``wl`` from V_loc and from the warm start (the same
+    mixer, Kerker-preconditioned unless ``kerker`` is None)."""
     import torch
     s = synth.make_system(wl)
     solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=device)
     V_loc = torch.from_numpy(s.V.ravel().copy()).to(device)
-    scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=beta, history=history, margin=wl.margin)
+    scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=beta, history=history, margin=wl.margin, kerker=kerker)
     t0 = time.perf_counter()
     plain = scf.run(tol=tol, max_iter=max_iter)
     t_plain = time.perf_counter() - t0
