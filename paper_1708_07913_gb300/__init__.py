@@ -300,17 +300,18 @@ class SQCNN:
 
 
 def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4, beta=0.3, history=7,
-                         poisson_tol=1e-10):
+                         poisson_tol=1e-10, kerker=None):
     """The SCF's starting potential from the learned network: the fixed
     point of V_in -> rho = net(V_in) -> V_out = V_loc + phi[rho] + v_x(rho)
     (the SCF map with the network in place of the SQ solve, Anderson-mixed,
-    at most ``iters`` steps or until ||V_out - V_in|| <= tol ||V_out||).
+    Kerker-preconditioned if ``kerker`` = (k0, amin) is given, at most
+    ``iters`` steps or until ||V_out - V_in|| <= tol ||V_out||).
     Returns (V_in, residuals); every step runs in libsq."""
     torch = solver.torch
     shape = solver.shape
     f64 = dict(dtype=torch.float64, device=solver.device)
     V_in, V_next = V_loc.clone(), torch.empty(solver.n_nodes, **f64)
-    rho, phi, V_out = (torch.empty(solver.n_nodes, **f64) for _ in range(3))
+    rho, phi, V_out, V_pre = (torch.empty(solver.n_nodes, **f64) for _ in range(4))
     with torch.cuda.device(solver.device):
         mixer = sq.sq_mixer_create(solver.n_nodes, history, beta)
     res = []
@@ -320,7 +321,12 @@ def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4
             net.predict(shape, V_in, out=rho)
             sq.sq_poisson(solver.ctx, rho, phi, poisson_tol)
             sq.sq_effective_potential(solver.ctx, V_loc, phi, rho, alpha, V_out)
-            res.append(sq.sq_mixer_step(mixer, V_in, V_out, V_next))
+            if kerker is None:
+                res.append(sq.sq_mixer_step(mixer, V_in, V_out, V_next))
+            else:
+                r, _ = sq.sq_kerker(solver.ctx, V_in, V_out, kerker[0], kerker[1], V_pre)
+                sq.sq_mixer_step(mixer, V_in, V_pre, V_next)
+                res.append(r)
             V_in, V_next = V_next, V_in
             if res[-1] <= tol:
                 break
