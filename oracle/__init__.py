@@ -315,7 +315,7 @@ _kerker = kerker      # the scf() argument of the same name shadows it there
 
 def scf(V_loc, h, m, positions, proj_types, n_electrons, kT, npl, alpha=2.0 / 3.0, beta=0.3, history=7,
         tol=1e-6, max_iter=60, n_lanczos=40, margin=0.01, periodic=False, fd_half_order=6, poisson_tol=1e-12,
-        kerker=None):
+        kerker=None, period=1):
     """The SCF loop of Section 3 around the SQ path, with the effective
     potential as the fixed-point variable: V_in -> SQ density rho[V_in] ->
     V_out = V_loc + phi[rho] + v_x[rho] (phi: Eq. PoissonEqn with a
@@ -323,8 +323,11 @@ def scf(V_loc, h, m, positions, proj_types, n_electrons, kT, npl, alpha=2.0 / 3.
     ||V_out - V_in|| <= tol ||V_out|| (2-norms); Anderson mixing with the last
     `history` differences.  Starts from V_in = V_loc.  ``kerker`` = (k0, amin)
     mixes the preconditioned residual P f (or_kerker) in place of f; the
-    stopping test stays on f.  Returns a dict with the converged V_in, rho,
-    mu, energies, the residual history and iterations."""
+    stopping test stays on f.  ``period`` = p > 1 is Periodic Pulay mixing
+    (Section 3): the Anderson (Pulay) extrapolation on every p-th step
+    (steps p-1, 2p-1, ... counting from 0), simple mixing x + beta f on the
+    others, the history kept throughout.  Returns a dict with the converged
+    V_in, rho, mu, energies, the residual history and iterations."""
     V_loc = _f64(V_loc)
     V_in = V_loc.copy()
     Xs, Fs, res = [], [], []
@@ -345,6 +348,9 @@ def scf(V_loc, h, m, positions, proj_types, n_electrons, kT, npl, alpha=2.0 / 3.
         Xs.append(V_in.ravel().copy())
         Fs.append(f.copy())
         Xs, Fs = Xs[-(history + 1):], Fs[-(history + 1):]
-        V_in = anderson_step(np.array(Xs), np.array(Fs), beta).reshape(V_loc.shape)
+        if (it + 1) % period == 0:
+            V_in = anderson_step(np.array(Xs), np.array(Fs), beta).reshape(V_loc.shape)
+        else:
+            V_in = anderson_step(np.array(Xs[-1:]), np.array(Fs[-1:]), beta).reshape(V_loc.shape)
     return dict(V=V_in, rho=out["rho"].reshape(V_loc.shape), mu=out["mu"], residuals=res, iterations=max_iter,
                 converged=False)

@@ -155,8 +155,10 @@ def test_scf_reaches_the_dense_diagonalisation_fixed_point():
     V_loc = synth.local_potential(n, L, pos)
     Ne, kT = 12.0, 0.5
     V_ref, rho_ref, mu_ref = _dense_scf(V_loc, h, Ne, kT)
-    for kerker in (None, (1.0, 0.2)):           # the fixed point does not depend on the preconditioner
-        r = oracle.scf(V_loc, h, 0, pos, (), Ne, kT, npl=100, tol=1e-8, periodic=True, n_lanczos=60, kerker=kerker)
+    # the fixed point depends neither on the preconditioner nor on the mixing schedule
+    for kerker, period in ((None, 1), ((1.0, 0.2), 1), (None, 3)):
+        r = oracle.scf(V_loc, h, 0, pos, (), Ne, kT, npl=100, tol=1e-8, periodic=True, n_lanczos=60, kerker=kerker,
+                       period=period)
         assert r["converged"] and r["iterations"] < 40
         assert r["residuals"][-1] <= 1e-8 < r["residuals"][0]
         np.testing.assert_allclose(r["V"], V_ref, atol=1e-6 * np.abs(V_ref).max())
