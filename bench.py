@@ -13,7 +13,7 @@ projectors, 324 electrons; synthetic, seeded inputs.
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
                   [--impl reference]
   python bench.py --workload batch16          (16 uneven systems as one CUDA graph)
-  python bench.py --workload force_al108_48   (nonlocal atomic forces, FP64)
+  python bench.py --workload force_al108_48   (nonlocal atomic forces; --precision fp32|fp64)
   python bench.py --workload warmstart_c4     (train the warm-start network, then SCF
                                                iterations to 1e-6 on al256_64 with and without it)
 
@@ -248,6 +248,23 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+def replica_times(times, dist):
+    """Each timing (seconds) maximised over the ranks (the slowest replica
+    sets the job's time); unchanged on one rank (dist None)."""
+    if dist is None:
+        return [float(t) for t in times]
+    import torch
+    tt = torch.tensor([float(t) for t in times], dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return [float(x) for x in tt]
+
+
+def replica_value(units_per_rank, world, t_max):
+    """Whole-job throughput: the units every rank processed over the
+    slowest rank's time."""
+    return units_per_rank * world / t_max
+
+
 def run_gb300(a):
     import torch
     from paper_1708_07913_gb300 import SQ_FP32, SQ_FP64, SQSolver, build
@@ -325,12 +342,9 @@ def run_gb300(a):
     step_ms = per.sum(axis=1)
     t_step = float(step_ms.mean()) / 1e3
     t_e2e = float(np.median(e2e_t))
-    if dist:
-        tt = torch.tensor([t_step, t_e2e], dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, t_e2e = float(tt[0]), float(tt[1])
+    t_step, t_e2e = replica_times([t_step, t_e2e], dist)
     units = wl.n_nodes * wl.npl * world
-    value = units / t_step
+    value = replica_value(wl.n_nodes * wl.npl, world, t_step)
     t_bounds, t_mom, t_fermi, t_dens = (float(x) / 1e3 for x in per.mean(axis=0))
 
     # roofline for the dominant kernel (FP32/FP64 CUDA-core pipe, "alu" bound)
@@ -531,11 +545,12 @@ def _oracle_force_chunk(nodes):
 
 
 def run_force(a):
-    """Nonlocal atomic forces (sq_nl_forces, FP64) on the workload named
-    after ``force_``, with the spectral bounds and Fermi level of one SQ
-    step computed first (not timed).  One step = one force evaluation."""
+    """Nonlocal atomic forces (sq_nl_forces; recurrence in the --precision
+    given, FP32 by default) on the workload named after ``force_``, with the
+    spectral bounds and Fermi level of one SQ step computed first (not
+    timed).  One step = one force evaluation."""
     import torch
-    from paper_1708_07913_gb300 import SQ_FP64, SQSolver, build
+    from paper_1708_07913_gb300 import SQ_FP32, SQ_FP64, SQSolver, build
 
     name = a.workload[len("force_"):]
     dev = torch.device("cuda:0")
@@ -543,7 +558,8 @@ def run_force(a):
     build()
     s = synth.make_system(name)
     wl = s.wl
-    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=str(dev))
+    prec = SQ_FP32 if a.precision == "fp32" else SQ_FP64
+    solver = SQSolver.from_workload(wl, s.positions, precision=prec, device=str(dev))
     Vh = torch.from_numpy(s.V.ravel().copy()).pin_memory()
     V = Vh.to(dev)
     out = solver.solve(V, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)
@@ -590,21 +606,27 @@ def run_force(a):
     peaks = json.load(open(PEAKS_PATH)) if os.path.exists(PEAKS_PATH) else {}
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = 1.25 * sms / SM_COUNT_GB300 * sm_max / 2070.0
+    if prec == SQ_FP32:
+        peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+        basis = f"FP32 CUDA-core pipe at {sm_max:.0f} MHz x {sms} SMs (derived from unit counts and clock)"
+    else:
+        peak = 1.25 * sms / SM_COUNT_GB300 * sm_max / 2070.0
+        basis = f"FP64 at GB300's published 1.25 TFLOP/s scaled to {sm_max:.0f} MHz x {sms} SMs"
     line = {
         "metric": FORCE_METRIC, "value": units / t, "unit": FORCE_UNIT, "n_gpus": 1, "steps": a.steps,
         "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64",
+        "vs_baseline": None, "dtype": "f32" if prec == SQ_FP32 else "f64",
         "data": "synthetic (seeded FCC Al-like crystal, Gaussian V and KB projectors)",
         "config": {"workload": f"{a.workload}: nonlocal forces on {name} ({wl.n_atoms} atoms, {wl.n}^3 grid, "
                                f"{S}^3 regions, n_pl={wl.npl}, kT={wl.kT}); {nt} of {wl.n_nodes} nodes inside "
                                f"a projector support",
-                   "precision": "FP64 throughout", "l2": "flushed between timed steps (256 MB write)",
+                   "precision": ("FP32 recurrence, D and projector sums; FP64 coefficients and contraction"
+                                 if prec == SQ_FP32 else "FP64 throughout"),
+                   "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "single GPU"},
         "forces_max_abs": float(F.abs().max().item()),
         "roofline": {"kernel": "nl_force_kernel", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
-                     "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None,
-                     "peak_basis": f"FP64 at GB300's published 1.25 TFLOP/s scaled to {sm_max:.0f} MHz x {sms} SMs"},
+                     "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None, "peak_basis": basis},
         "e2e": {"value": units / float(np.median(e2e)), "unit": FORCE_UNIT,
                 "h2d_bytes_per_step": 3 * wl.n_nodes * 8, "d2h_bytes_per_step": wl.n_atoms * 3 * 8},
         "gpu_launches": int(launches),
