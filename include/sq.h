@@ -190,10 +190,14 @@ int sq_density_energy_noalloc(int n1, int n2, int n3, double h, int npl,
  *   mu, kT     Fermi level (e.g. from sq_fermi_level) and smearing > 0, Ha
  *   forces     device, n_atoms*3 FP64 output (Ha/bohr, atom-major x,y,z),
  *              overwritten; may be NULL when the context has no projectors
- * FP64 contexts only (SQ_EUNSUPPORTED otherwise).  The result repeats bit for
- * bit on a given GPU.  Allocates, on first use, about 2 x SMs x (32 (2m+1)^3
- * + 52 ccap + 24 n_atoms) bytes of workspace in the context.  Synchronises
- * the stream; a projector-table overflow returns SQ_ECAPACITY. */
+ * The recurrence vectors, D and the projector inner products are in the
+ * context's precision (FP32 or FP64); the coefficients c^j and the final
+ * contraction are FP64.  The result repeats bit for bit on a given GPU.
+ * Allocates, on first use, about 2 x SMs x (4 s (2m+1)^3 + (384 + 128 s)
+ * (2m+1)^2 + (24 + 4 s) ccap + 24 n_atoms) bytes of workspace in the context
+ * (s = 4 or 8 bytes).  A region row crossed by more than 32 projector
+ * supports returns SQ_ECAPACITY.
+ * Synchronises the stream; a projector-table overflow returns SQ_ECAPACITY. */
 int sq_nl_forces(sq_ctx *ctx, const double *V, const double *chi, const double *zeta,
                  double mu, double kT, double *forces);
 
@@ -290,12 +294,19 @@ void sq_batch_destroy(sq_batch *b);
  *   gamma minimising ||f - dF gamma|| over the stored differences (if their
  *   normal equations are numerically singular the history is not used).
  *   Device vectors of n doubles.  Synchronises the mixer's stream.
+ * sq_mixer_set_period(mx, period, steps_done): Periodic Pulay mixing (the
+ *   paper's scheme, Section 3): the extrapolation above on steps period-1,
+ *   2 period-1, ... (counting steps from 0) and simple mixing v_in + beta f
+ *   on the others, the history recorded on every step; steps_done sets the
+ *   step count (0 for a new loop, the steps already taken when resuming).
+ *   1 <= period <= 1000 (1, the default, extrapolates on every step).
  * sq_mixer_history(mx, count_host): pairs currently stored (0..history+1).
  * sq_mixer_export(mx, X_host, F_host): copy the stored iterates and residuals,
  *   oldest first, into HOST arrays of count x n doubles each (for a
  *   checkpoint).  sq_mixer_import(mx, count, X_host, F_host): replace the
  *   history by count <= history + 1 such pairs (resuming from a checkpoint).
- * sq_mixer_reset(mx): forget the history.  sq_mixer_destroy(mx): release.
+ * sq_mixer_reset(mx): forget the history and the step count.
+ * sq_mixer_destroy(mx): release.
  * ------------------------------------------------------------------------- */
 int sq_poisson(sq_ctx *ctx, const double *rho, double *phi, double tol, int max_iter,
                int *iters_host, double *rel_resid_host);
@@ -307,6 +318,7 @@ typedef struct sq_mixer sq_mixer;
 int sq_mixer_create(sq_mixer **out, long long n, int history, double beta, void *cuda_stream);
 int sq_mixer_step(sq_mixer *mx, const double *v_in, const double *v_out, double *v_next,
                   double *rel_resid_host);
+int sq_mixer_set_period(sq_mixer *mx, int period, long long steps_done);
 int sq_mixer_history(const sq_mixer *mx, int *count_host);
 int sq_mixer_export(sq_mixer *mx, double *X_host, double *F_host);
 int sq_mixer_import(sq_mixer *mx, int count, const double *X_host, const double *F_host);

@@ -154,13 +154,15 @@ class SQSCF:
     sequences them."""
 
     def __init__(self, solver, V_loc, n_electrons, kT, alpha=2.0 / 3.0, beta=0.3, history=7, n_lanczos=40,
-                 margin=0.01, kerker=None):
+                 margin=0.01, kerker=None, period=1):
         """``kerker`` = (k0, amin): mix the Kerker-preconditioned residual
         (sq_kerker) in place of V_out - V_in; the stopping test stays on the
-        unpreconditioned residual."""
+        unpreconditioned residual.  ``period`` = p > 1: Periodic Pulay
+        mixing (extrapolation on every p-th step, simple mixing between)."""
         torch = solver.torch
         self.solver, self.V_loc = solver, V_loc
         self.kerker = None if kerker is None else (float(kerker[0]), float(kerker[1]))
+        self.period = int(period)
         self.n_electrons, self.kT, self.alpha = float(n_electrons), float(kT), float(alpha)
         self.n_lanczos, self.margin = int(n_lanczos), float(margin)
         f64 = dict(dtype=torch.float64, device=solver.device)
@@ -192,6 +194,7 @@ class SQSCF:
             res = list(ck["residuals"])
         else:
             V_in.copy_(self.V_loc if V0 is None else V0)
+        sq.sq_mixer_set_period(self.mixer, self.period, len(res))
         for it in range(len(res), max_iter):
             out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
             if on_step is not None:

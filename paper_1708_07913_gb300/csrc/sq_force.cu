@@ -45,18 +45,23 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 // Byte offsets of the per-CTA slices inside one CTA's part of the workspace.
 struct ForceLayout {
-    size_t vec, cand, clen, P, F, total;
+    size_t vec, cand, clen, P, rowent, rown, cent, cstart, part, F, total;
 };
 
-ForceLayout force_layout(int S, int cap, int n_atoms)
+ForceLayout force_layout(int S, int cap, int n_atoms, size_t tsz)
 {
     ForceLayout L;
-    const size_t S3 = (size_t)S * S * S;
+    const size_t S2 = (size_t)S * S, S3 = S2 * S;
     L.vec = 0;
-    L.cand = L.vec + align256(sizeof(double) * 4 * S3);
+    L.cand = L.vec + align256(tsz * 4 * S3);
     L.clen = L.cand + align256(sizeof(int4) * cap);
     L.P = L.clen + align256(sizeof(int) * cap);
-    L.F = L.P + align256(sizeof(double) * 4 * cap);
+    L.rowent = L.P + align256(tsz * 4 * cap);
+    L.rown = L.rowent + align256(sizeof(int2) * S2 * FORCE_EPR);
+    L.cent = L.rown + align256(sizeof(int) * S2);
+    L.cstart = L.cent + align256(sizeof(int) * S2 * FORCE_EPR);
+    L.part = L.cstart + align256(sizeof(int) * (cap + 1));
+    L.F = L.part + align256(tsz * 4 * S2 * FORCE_EPR);
     L.total = L.F + align256(sizeof(double) * 3 * (size_t)n_atoms);
     return L;
 }
@@ -79,6 +84,60 @@ void ws_release(ForceWS* w)
     delete w;
 }
 
+// Arguments and launch of the force kernel in precision T (the context's
+// recurrence precision), then the fixed-order sum over its CTAs.
+template <typename T>
+int launch_force(sq_ctx* c, const ForceLayout& L, char* base, int blocks, const double* chi, const double* zeta,
+                 double mu, double kT, double* forces)
+{
+    ForceArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.g = c->g;
+    a.lap[0] = (T)(-3.0 * c->g.w[0]);
+    for (int d = 1; d <= FD_NO; ++d) a.lap[d] = (T)(-0.5 * c->g.w[d]);
+    grad_weights(FD_NO, c->g.h, a.grad);
+    a.Vp = (const T*)c->Vp;
+    a.nl.n_atoms = c->n_atoms;
+    a.nl.atoms = c->d_atoms;
+    a.nl.lb = c->lb;
+    a.nl.G = (const T*)c->d_G;
+    a.nl.DG = (const T*)c->d_DG;
+    a.nl.ivl = c->d_ivl;
+    a.nl.tile_start = c->d_tile_start;
+    a.nl.tile_cand = c->d_tile_cand;
+    for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
+    a.nl.ccap = c->ccap;
+    a.nl.smem = 0;
+    const double h3 = c->g.h * c->g.h * c->g.h;
+    const double As2 = pow(M_PI * c->rc * c->rc, -1.5);          // A_s^2
+    const double Ap2 = 2.0 / (c->rc * c->rc) * As2;              // A_p^2
+    a.nl.cs = (T)(c->has_s ? h3 * c->gamma_s * As2 : 0.0);
+    a.nl.cp = (T)(c->has_p ? h3 * c->gamma_p * Ap2 : 0.0);
+    a.chi = chi;
+    a.zeta = zeta;
+    a.mu = mu;
+    a.kT = kT;
+    a.npl = c->npl;
+    // the per-CTA slices are grouped by kind: all CTAs' vectors, then all
+    // candidate lists, ... (each kind contiguous, CTA b at offset b * size)
+    a.vec = (T*)(base + L.vec * blocks);
+    a.cand = (int4*)(base + L.cand * blocks);
+    a.clen = (int*)(base + L.clen * blocks);
+    a.P = (T*)(base + L.P * blocks);
+    a.rowent = (int2*)(base + L.rowent * blocks);
+    a.rown = (int*)(base + L.rown * blocks);
+    a.cent = (int*)(base + L.cent * blocks);
+    a.cstart = (int*)(base + L.cstart * blocks);
+    a.part = (T*)(base + L.part * blocks);
+    a.Fcta = (double*)(base + L.F * blocks);
+    a.err = c->d_err;
+    nl_force_kernel<T><<<blocks, FORCE_NT, 0, c->stream>>>(a);
+    if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    const int n3 = 3 * c->n_atoms;
+    force_sum_kernel<<<(n3 + 127) / 128, 128, 0, c->stream>>>(a.Fcta, blocks, n3, forces);
+    return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;
+}
+
 }  // namespace
 
 namespace sq {
@@ -99,14 +158,14 @@ extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const
     if (!c || !isfinite(mu) || !isfinite(kT) || kT <= 0.0) return SQ_EINVAL;
     if (!dev_ptr(V) || !dev_ptr(chi) || !dev_ptr(zeta)) return SQ_EINVAL;
     if (c->n_atoms > 0 && !dev_ptr(forces)) return SQ_EINVAL;
-    if (c->precision != SQ_FP64) return SQ_EUNSUPPORTED;
     if (c->n_atoms == 0) return SQ_OK;
     const int n3 = 3 * c->n_atoms;
     if (!c->has_s && !c->has_p)
         return cudaMemsetAsync(forces, 0, sizeof(double) * n3, c->stream) == cudaSuccess ? SQ_OK : SQ_ECUDA;
 
     const int S = 2 * c->g.m + 1;
-    const ForceLayout L = force_layout(S, c->ccap, c->n_atoms);
+    const size_t tsz = c->precision == SQ_FP32 ? sizeof(float) : sizeof(double);
+    const ForceLayout L = force_layout(S, c->ccap, c->n_atoms, tsz);
     const int blocks = (int)std::min<long long>(c->g.Nd, 2LL * c->sm_count);
     const size_t need = L.total * (size_t)blocks;
     ForceWS* ws = nullptr;
@@ -137,49 +196,9 @@ extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const
 
     int rc = launch_build_vpad(c, V);
     if (rc) return rc;
-
-    // the per-CTA slices are interleaved by kind: all CTAs' vectors, then all
-    // candidate lists, ... (each kind contiguous, CTA b at offset b * size)
-    ForceArgs a;
-    memset(&a, 0, sizeof(a));
-    a.g = c->g;
-    a.lap[0] = -3.0 * c->g.w[0];
-    for (int d = 1; d <= FD_NO; ++d) a.lap[d] = -0.5 * c->g.w[d];
-    grad_weights(FD_NO, c->g.h, a.grad);
-    a.Vp = (const double*)c->Vp;
-    a.nl.n_atoms = c->n_atoms;
-    a.nl.atoms = c->d_atoms;
-    a.nl.lb = c->lb;
-    a.nl.G = (const double*)c->d_G;
-    a.nl.DG = (const double*)c->d_DG;
-    a.nl.ivl = c->d_ivl;
-    a.nl.tile_start = c->d_tile_start;
-    a.nl.tile_cand = c->d_tile_cand;
-    for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
-    a.nl.ccap = c->ccap;
-    a.nl.smem = 0;
-    const double h3 = c->g.h * c->g.h * c->g.h;
-    const double As2 = pow(M_PI * c->rc * c->rc, -1.5);          // A_s^2
-    const double Ap2 = 2.0 / (c->rc * c->rc) * As2;              // A_p^2
-    a.nl.cs = c->has_s ? h3 * c->gamma_s * As2 : 0.0;
-    a.nl.cp = c->has_p ? h3 * c->gamma_p * Ap2 : 0.0;
-    a.chi = chi;
-    a.zeta = zeta;
-    a.mu = mu;
-    a.kT = kT;
-    a.npl = c->npl;
-    char* base = ws->buf;
-    a.vec = (double*)(base + L.vec * blocks);
-    a.cand = (int4*)(base + L.cand * blocks);
-    a.clen = (int*)(base + L.clen * blocks);
-    a.P = (double*)(base + L.P * blocks);
-    a.Fcta = (double*)(base + L.F * blocks);
-    a.err = c->d_err;
-
-    nl_force_kernel<<<blocks, FORCE_NT, 0, c->stream>>>(a);
-    if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
-    force_sum_kernel<<<(n3 + 127) / 128, 128, 0, c->stream>>>(a.Fcta, blocks, n3, forces);
-    if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    rc = c->precision == SQ_FP32 ? launch_force<float>(c, L, ws->buf, blocks, chi, zeta, mu, kT, forces)
+                                 : launch_force<double>(c, L, ws->buf, blocks, chi, zeta, mu, kT, forces);
+    if (rc) return rc;
     c->launches += 2;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
     unsigned e = 0;

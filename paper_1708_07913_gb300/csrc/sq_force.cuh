@@ -13,16 +13,24 @@
 // nodes inside the support of some projector contribute.
 //
 // One CTA per node (persistent grid).  The three recurrence vectors and D
-// live in per-CTA global scratch; every step is two block-wide phases:
-//   (a) the local part of H (stencil + V) at every region point, and the
-//       projector inner products <chi_c, t> with one thread per candidate
-//       (support rows in z, y, x order);
-//   (b) the projector update, the shift/scale to Hhat, the three-term step
-//       and D += c^j t^{j+1}.
+// live in per-CTA global scratch.  Per node, every region row (y, z) gets
+// the list of candidate images whose support crosses it (x-interval and
+// box-relative row), and every candidate the list of its row entries in row
+// order.  Every step is three block-wide phases:
+//   (a) the local part of H (stencil + V) at every region point, and, one
+//       thread per row, the partial inner products <chi_c, t> of each of the
+//       row's entries;
+//   (a2) one thread per candidate: its inner products, the partials of its
+//       entries added in row order;
+//   (b) the projector update (a point visits its row's entries only), the
+//       shift/scale to Hhat, the three-term step and D += c^j t^{j+1}.
 // The contribution of each (node, candidate image) pair is added to a
 // per-CTA force array in candidate order by one thread, and a second kernel
 // adds the CTA arrays in block order: the result repeats bit for bit for a
-// given grid.  FP64 only.
+// given grid.  T is the context's recurrence precision: the three vectors,
+// D, the projector inner products and the potential/projector tables are in
+// T; the interpolation coefficients and the final contraction (the gradient
+// sums and the force) are in FP64.
 //
 // The code uses block barriers and plain loads/stores only (no warp
 // intrinsics), every loop has a fixed trip count, and every table index is
@@ -33,23 +41,30 @@
 namespace sq {
 
 constexpr int FORCE_NT = 256;        // threads per CTA of the force kernel
+constexpr int FORCE_EPR = 32;        // projector entries a region row may hold
 
+template <typename T>
 struct ForceArgs {
     GridParams g;
-    double lap[FD_NO + 1];           // lap[0] = -3 w_0 (diagonal), lap[d] = -w_d/2 (d >= 1)
+    T lap[FD_NO + 1];                // lap[0] = -3 w_0 (diagonal), lap[d] = -w_d/2 (d >= 1)
     double grad[FD_NO + 1];          // gradient weights of Eq. FD:Gradient, d = 1..n_o
-    const double* Vp;                // potential with a periodic halo of m points
-    NLParams<double> nl;
+    const T* Vp;                     // potential with a periodic halo of m points
+    NLParams<T> nl;
     const double* chi;
     const double* zeta;
     double mu;
     double kT;
     int npl;
     // per-CTA scratch (slices of the sizes given)
-    double* vec;                     // 4 S^3 per CTA: t^{j-1}, t^j, t^{j+1}, D
+    T* vec;                          // 4 S^3 per CTA: t^{j-1}, t^j, t^{j+1}, D
     int4* cand;                      // ccap per CTA: (atom, box start relative to the region)
     int* clen;                       // ccap per CTA: box lengths len_x | len_y << 8 | len_z << 16
-    double* P;                       // 4 ccap per CTA: <chi_s, t>, <chi_px, t>, <chi_py, t>, <chi_pz, t>
+    T* P;                            // 4 ccap per CTA: <chi_s, t>, <chi_px, t>, <chi_py, t>, <chi_pz, t>
+    int2* rowent;                    // S^2 FORCE_EPR per CTA: (c | xlo << 10 | xhi << 15, jj | kk << 8)
+    int* rown;                       // S^2 per CTA: entries of each row
+    int* cent;                       // S^2 FORCE_EPR per CTA: entry indices r FORCE_EPR + e of each candidate
+    int* cstart;                     // ccap + 1 per CTA: candidate c owns cent[cstart[c] .. cstart[c+1])
+    T* part;                         // 4 S^2 FORCE_EPR per CTA: partial inner products of each entry
     double* Fcta;                    // 3 n_atoms per CTA
     unsigned* err;
 };
@@ -60,7 +75,8 @@ __device__ inline int fmax_i(int a, int b) { return a > b ? a : b; }
 // Region row (y, z) of candidate cr: its support x-interval [xlo, xhi] in
 // region columns and the box-relative row (jj, kk); false if the row misses
 // the box or the support.
-__device__ inline bool force_row(const NLParams<double>& nl, int4 cr, int ln, int S, int y, int z, int& xlo,
+template <typename T>
+__device__ inline bool force_row(const NLParams<T>& nl, int4 cr, int ln, int S, int y, int z, int& xlo,
                                  int& xhi, int& jj, int& kk)
 {
     jj = y - cr.z;
@@ -74,23 +90,37 @@ __device__ inline bool force_row(const NLParams<double>& nl, int4 cr, int ln, in
     return xlo <= xhi;
 }
 
+// Per-CTA views of the row and candidate entry lists.
+template <typename T>
+struct ForceLists {
+    const int4* cand;
+    const int* clen;
+    int ncand;
+    const int2* rowent;
+    const int* rown;
+    const int* cent;
+    const int* cstart;
+    T* part;
+    T* P;
+};
+
 // One step y = Hhat x (xm == nullptr) or y = 2 Hhat x - xm, then D += cj y.
-__device__ inline void force_hhat(const ForceArgs& a, int qi, int qj, int qk, int S, double chq, double zq,
-                                  const int4* cand, const int* clen, int ncand, double* P, const double* x,
-                                  const double* xm, double* y, double* D, double cj)
+template <typename T>
+__device__ inline void force_hhat(const ForceArgs<T>& a, int qi, int qj, int qk, int S, T chq, T zq,
+                                  const ForceLists<T>& L, const T* x, const T* xm, T* y, T* D, T cj)
 {
     const int tid = threadIdx.x;
     const long long S2 = (long long)S * S, S3 = S2 * S;
-    const NLParams<double>& nl = a.nl;
+    const NLParams<T>& nl = a.nl;
     const int lb = nl.lb;
-    // (a) local part and projector inner products
+    // (a) local part, and the partial inner products of every row entry
     for (long long p = tid; p < S3; p += FORCE_NT) {
         const int px = (int)(p % S), py = (int)((p / S) % S), pz = (int)(p / S2);
-        const double v = a.Vp[(long long)(qi + px) +
-                              (long long)a.g.P1 * ((long long)(qj + py) + (long long)a.g.P2 * (qk + pz))];
-        double acc = (a.lap[0] + v) * x[p];
+        const T v = a.Vp[(long long)(qi + px) +
+                         (long long)a.g.P1 * ((long long)(qj + py) + (long long)a.g.P2 * (qk + pz))];
+        T acc = (a.lap[0] + v) * x[p];
         for (int d = 1; d <= FD_NO; ++d) {
-            double nb = 0.0;
+            T nb = 0;
             if (px + d < S) nb += x[p + d];
             if (px - d >= 0) nb += x[p - d];
             if (py + d < S) nb += x[p + (long long)d * S];
@@ -101,61 +131,79 @@ __device__ inline void force_hhat(const ForceArgs& a, int qi, int qj, int qk, in
         }
         y[p] = acc;
     }
-    for (int c = tid; c < ncand; c += FORCE_NT) {
-        const int4 cr = cand[c];
-        const int ln = clen[c];
-        const double* Gt = nl.G + (size_t)cr.x * 3 * lb;
-        const double* Dt = nl.DG + (size_t)cr.x * 3 * lb;
-        double ss = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
-        const int z0 = fmax_i(cr.w, 0), z1 = fmin_i(cr.w + ((ln >> 16) & 255), S);
-        const int y0 = fmax_i(cr.z, 0), y1 = fmin_i(cr.z + ((ln >> 8) & 255), S);
-        for (int z = z0; z < z1; ++z)
-            for (int yy = y0; yy < y1; ++yy) {
-                int xlo, xhi, jj, kk;
-                if (!force_row(nl, cr, ln, S, yy, z, xlo, xhi, jj, kk)) continue;
-                const double gy = Gt[lb + jj], dgy = Dt[lb + jj], gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
-                const double* xr = x + ((long long)yy + (long long)S * z) * S;
-                for (int xx = xlo; xx <= xhi; ++xx) {
-                    const int ii = xx - cr.y;
-                    const double v = xr[xx], gx = Gt[ii], dgx = Dt[ii];
-                    ss += gx * gy * gz * v;
-                    sx += dgx * gy * gz * v;
-                    sy += gx * dgy * gz * v;
-                    sz += gx * gy * dgz * v;
-                }
+    for (int r = tid; r < S * S; r += FORCE_NT) {
+        const int n = L.rown[r];
+        const T* xr = x + (long long)r * S;
+        for (int e = 0; e < n; ++e) {
+            const int2 en = L.rowent[r * FORCE_EPR + e];
+            const int c = en.x & 1023, xlo = (en.x >> 10) & 31, xhi = (en.x >> 15) & 31;
+            const int jj = en.y & 255, kk = (en.y >> 8) & 255;
+            const int4 cr = L.cand[c];
+            const T* Gt = nl.G + (size_t)cr.x * 3 * lb;
+            const T* Dt = nl.DG + (size_t)cr.x * 3 * lb;
+            T sg = 0, sd = 0;
+            for (int xx = xlo; xx <= xhi; ++xx) {
+                const T v = xr[xx];
+                sg += Gt[xx - cr.y] * v;
+                sd += Dt[xx - cr.y] * v;
             }
-        P[4 * c + 0] = ss;
-        P[4 * c + 1] = sx;
-        P[4 * c + 2] = sy;
-        P[4 * c + 3] = sz;
+            const T gy = Gt[lb + jj], dgy = Dt[lb + jj], gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
+            T* o = L.part + 4 * ((size_t)r * FORCE_EPR + e);
+            o[0] = gy * gz * sg;
+            o[1] = gy * gz * sd;
+            o[2] = dgy * gz * sg;
+            o[3] = gy * dgz * sg;
+        }
     }
     __syncthreads();
-    // (b) projector update, Hhat, three-term step, D
-    const double cs = nl.cs, cp = nl.cp;
-    for (long long p = tid; p < S3; p += FORCE_NT) {
-        const int px = (int)(p % S), py = (int)((p / S) % S), pz = (int)(p / S2);
-        double acc = y[p];
-        for (int c = 0; c < ncand; ++c) {
-            const int4 cr = cand[c];
-            int xlo, xhi, jj, kk;
-            if (!force_row(nl, cr, clen[c], S, py, pz, xlo, xhi, jj, kk) || px < xlo || px > xhi) continue;
-            const int ii = px - cr.y;
-            const double* Gt = nl.G + (size_t)cr.x * 3 * lb;
-            const double* Dt = nl.DG + (size_t)cr.x * 3 * lb;
-            const double gx = Gt[ii], dgx = Dt[ii], gy = Gt[lb + jj], dgy = Dt[lb + jj];
-            const double gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
-            acc += cs * P[4 * c] * (gx * gy * gz) +
-                   cp * (P[4 * c + 1] * (dgx * gy * gz) + P[4 * c + 2] * (gx * dgy * gz) + P[4 * c + 3] * (gx * gy * dgz));
+    // (a2) per candidate, its entries' partials in row order
+    for (int c = tid; c < L.ncand; c += FORCE_NT) {
+        T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+        for (int k = L.cstart[c]; k < L.cstart[c + 1]; ++k) {
+            const T* o = L.part + 4 * (size_t)L.cent[k];
+            s0 += o[0];
+            s1 += o[1];
+            s2 += o[2];
+            s3 += o[3];
         }
-        double v = (acc - chq * x[p]) / zq;
-        if (xm) v = 2.0 * v - xm[p];
+        L.P[4 * c + 0] = s0;
+        L.P[4 * c + 1] = s1;
+        L.P[4 * c + 2] = s2;
+        L.P[4 * c + 3] = s3;
+    }
+    __syncthreads();
+    // (b) projector update from the point's row entries, Hhat, three-term step, D
+    const T cs = nl.cs, cp = nl.cp;
+    for (long long p = tid; p < S3; p += FORCE_NT) {
+        const int px = (int)(p % S);
+        const int r = (int)(p / S);
+        T acc = y[p];
+        const int n = L.rown[r];
+        for (int e = 0; e < n; ++e) {
+            const int2 en = L.rowent[r * FORCE_EPR + e];
+            const int xlo = (en.x >> 10) & 31, xhi = (en.x >> 15) & 31;
+            if (px < xlo || px > xhi) continue;
+            const int c = en.x & 1023, jj = en.y & 255, kk = (en.y >> 8) & 255;
+            const int4 cr = L.cand[c];
+            const int ii = px - cr.y;
+            const T* Gt = nl.G + (size_t)cr.x * 3 * lb;
+            const T* Dt = nl.DG + (size_t)cr.x * 3 * lb;
+            const T gx = Gt[ii], dgx = Dt[ii], gy = Gt[lb + jj], dgy = Dt[lb + jj];
+            const T gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
+            const T* Pc = L.P + 4 * c;
+            acc += cs * Pc[0] * (gx * gy * gz) +
+                   cp * (Pc[1] * (dgx * gy * gz) + Pc[2] * (gx * dgy * gz) + Pc[3] * (gx * gy * dgz));
+        }
+        T v = (acc - chq * x[p]) / zq;
+        if (xm) v = (T)2 * v - xm[p];
         y[p] = v;
         D[p] += cj * v;
     }
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs a)
+template <typename T>
+__global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs<T> a)
 {
     __shared__ double s_fk[MAX_NPL + 1];     // Fermi function at the Chebyshev zeros
     __shared__ double s_th[MAX_NPL + 1];     // their angles
@@ -170,16 +218,22 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs a)
     const int tid = threadIdx.x;
     const int M = a.g.m, S = 2 * M + 1;
     const long long S3 = (long long)S * S * S;
-    const NLParams<double>& nl = a.nl;
+    const NLParams<T>& nl = a.nl;
     const int cap = nl.ccap;
     const int npl = a.npl;
-    double* tm = a.vec + (size_t)blockIdx.x * 4 * S3;
-    double* t = tm + S3;
-    double* tn = t + S3;
-    double* D = tn + S3;
+    T* tm = a.vec + (size_t)blockIdx.x * 4 * S3;
+    T* t = tm + S3;
+    T* tn = t + S3;
+    T* D = tn + S3;
     int4* cand = a.cand + (size_t)blockIdx.x * cap;
     int* clen = a.clen + (size_t)blockIdx.x * cap;
-    double* P = a.P + (size_t)blockIdx.x * 4 * cap;
+    T* P = a.P + (size_t)blockIdx.x * 4 * cap;
+    const int S2i = S * S;
+    int2* rowent = a.rowent + (size_t)blockIdx.x * S2i * FORCE_EPR;
+    int* rown = a.rown + (size_t)blockIdx.x * S2i;
+    int* cent = a.cent + (size_t)blockIdx.x * S2i * FORCE_EPR;
+    int* cstart = a.cstart + (size_t)blockIdx.x * (cap + 1);
+    T* part = a.part + (size_t)blockIdx.x * 4 * S2i * FORCE_EPR;
     double* Fc = a.Fcta + (size_t)blockIdx.x * 3 * nl.n_atoms;
     for (int i = tid; i < 3 * nl.n_atoms; i += FORCE_NT) Fc[i] = 0.0;
     const long long ctr = (long long)M + (long long)S * (M + (long long)S * M);
@@ -235,6 +289,57 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs a)
         }
         __syncthreads();
         if (!s_touch) continue;
+        // (2b) row entries (each row scans the candidates in order), then each
+        // candidate's entries in row order (counted, offsets, filled)
+        for (int r = tid; r < S2i; r += FORCE_NT) {
+            const int y = r % S, z = r / S;
+            int n = 0;
+            for (int c = 0; c < ncand; ++c) {
+                int xlo, xhi, jj, kk;
+                if (!force_row(nl, cand[c], clen[c], S, y, z, xlo, xhi, jj, kk)) continue;
+                if (n < FORCE_EPR) {
+                    rowent[r * FORCE_EPR + n] = make_int2(c | (xlo << 10) | (xhi << 15), jj | (kk << 8));
+                    ++n;
+                } else {
+                    atomicOr(a.err, ERR_CAPACITY);
+                }
+            }
+            rown[r] = n;
+        }
+        __syncthreads();
+        for (int c = tid; c < ncand; c += FORCE_NT) {
+            const int4 cr = cand[c];
+            const int ln = clen[c];
+            const int z0 = fmax_i(cr.w, 0), z1 = fmin_i(cr.w + ((ln >> 16) & 255), S);
+            const int y0 = fmax_i(cr.z, 0), y1 = fmin_i(cr.z + ((ln >> 8) & 255), S);
+            int cnt = 0;
+            for (int z = z0; z < z1; ++z)
+                for (int y = y0; y < y1; ++y) {
+                    const int r = y + S * z;
+                    for (int e = 0; e < rown[r]; ++e) cnt += (rowent[r * FORCE_EPR + e].x & 1023) == c;
+                }
+            cstart[c + 1] = cnt;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            cstart[0] = 0;
+            for (int c = 0; c < ncand; ++c) cstart[c + 1] += cstart[c];
+        }
+        __syncthreads();
+        for (int c = tid; c < ncand; c += FORCE_NT) {
+            const int4 cr = cand[c];
+            const int ln = clen[c];
+            const int z0 = fmax_i(cr.w, 0), z1 = fmin_i(cr.w + ((ln >> 16) & 255), S);
+            const int y0 = fmax_i(cr.z, 0), y1 = fmin_i(cr.z + ((ln >> 8) & 255), S);
+            int k = cstart[c];
+            for (int z = z0; z < z1; ++z)
+                for (int y = y0; y < y1; ++y) {
+                    const int r = y + S * z;
+                    for (int e = 0; e < rown[r]; ++e)
+                        if ((rowent[r * FORCE_EPR + e].x & 1023) == c) cent[k++] = r * FORCE_EPR + e;
+                }
+        }
+        const ForceLists<T> lists{cand, clen, ncand, rowent, rown, cent, cstart, part, P};
         // (3) c^j = (2/(n_pl+1)) sum_k g(chi + zeta x_k) T_j(x_k), c^0 halved
         const double chq = a.chi[q], zq = a.zeta[q];
         for (int k = tid; k <= npl; k += FORCE_NT) {
@@ -251,14 +356,15 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs a)
         __syncthreads();
         // (4) t^0 = e_q, D = c^0 t^0; the recurrence to n_pl accumulating D
         for (long long p = tid; p < S3; p += FORCE_NT) {
-            tm[p] = p == ctr ? 1.0 : 0.0;
-            D[p] = p == ctr ? s_c[0] : 0.0;
+            tm[p] = p == ctr ? (T)1 : (T)0;
+            D[p] = p == ctr ? (T)s_c[0] : (T)0;
         }
         __syncthreads();
-        force_hhat(a, qi, qj, qk, S, chq, zq, cand, clen, ncand, P, tm, nullptr, t, D, s_c[1]);
+        const T chT = (T)chq, zT = (T)zq;
+        force_hhat<T>(a, qi, qj, qk, S, chT, zT, lists, tm, nullptr, t, D, (T)s_c[1]);
         for (int j = 2; j <= npl; ++j) {
-            force_hhat(a, qi, qj, qk, S, chq, zq, cand, clen, ncand, P, t, tm, tn, D, s_c[j]);
-            double* r = tm;
+            force_hhat<T>(a, qi, qj, qk, S, chT, zT, lists, t, tm, tn, D, (T)s_c[j]);
+            T* r = tm;
             tm = t;
             t = tn;
             tn = r;
@@ -272,14 +378,15 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs a)
             double val = 0.0;
             int xlo, xhi, jj, kk;
             if (force_row(nl, cr, ln, S, M, M, xlo, xhi, jj, kk) && xlo <= M && M <= xhi) {
-                const double* Gt = nl.G + (size_t)cr.x * 3 * nl.lb;
-                const double* Dt = nl.DG + (size_t)cr.x * 3 * nl.lb;
+                const T* Gt = nl.G + (size_t)cr.x * 3 * nl.lb;
+                const T* Dt = nl.DG + (size_t)cr.x * 3 * nl.lb;
                 const int lb = nl.lb;
                 const int i0 = M - cr.y;
-                const double s0 = Gt[i0] * Gt[lb + jj] * Gt[2 * lb + kk];
-                const double x0 = Dt[i0] * Gt[lb + jj] * Gt[2 * lb + kk];
-                const double y0v = Gt[i0] * Dt[lb + jj] * Gt[2 * lb + kk];
-                const double z0v = Gt[i0] * Gt[lb + jj] * Dt[2 * lb + kk];
+                const double g0x = Gt[i0], g0y = Gt[lb + jj], g0z = Gt[2 * lb + kk];
+                const double s0 = g0x * g0y * g0z;
+                const double x0 = (double)Dt[i0] * g0y * g0z;
+                const double y0v = g0x * (double)Dt[lb + jj] * g0z;
+                const double z0v = g0x * g0y * (double)Dt[2 * lb + kk];
                 double ss = 0.0, sx = 0.0, sy = 0.0, sz = 0.0;
                 const int z0 = fmax_i(cr.w, 0), z1 = fmin_i(cr.w + ((ln >> 16) & 255), S);
                 const int y0 = fmax_i(cr.z, 0), y1 = fmin_i(cr.z + ((ln >> 8) & 255), S);
@@ -293,8 +400,8 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs a)
                             const long long p = (long long)xx + (long long)S * (yy + (long long)S * z);
                             double gd = 0.0;
                             for (int d = 1; d <= FD_NO; ++d) {
-                                const double dp = pc[ax] + d < S ? D[p + d * sa[ax]] : 0.0;
-                                const double dm = pc[ax] - d >= 0 ? D[p - d * sa[ax]] : 0.0;
+                                const double dp = pc[ax] + d < S ? (double)D[p + d * sa[ax]] : 0.0;
+                                const double dm = pc[ax] - d >= 0 ? (double)D[p - d * sa[ax]] : 0.0;
                                 gd += a.grad[d] * (dp - dm);
                             }
                             const int ii = xx - cr.y;
@@ -305,7 +412,7 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs a)
                             sz += gx * gy * dgz * gd;
                         }
                     }
-                val = -4.0 * (nl.cs * s0 * ss + nl.cp * (x0 * sx + y0v * sy + z0v * sz));
+                val = -4.0 * ((double)nl.cs * s0 * ss + (double)nl.cp * (x0 * sx + y0v * sy + z0v * sz));
             }
             s_f[task] = val;
         }

@@ -327,6 +327,8 @@ struct sq_mixer {
     long long n = 0;
     int hist = 0;
     double beta = 0.0;
+    int period = 1;              // Pulay extrapolation on every period-th step (1: every step)
+    long long steps = 0;         // steps taken (decides the Pulay steps)
     cudaStream_t st = nullptr;
     int sm = 1;
     std::vector<double*> X, F;   // hist + 1 slots each
@@ -560,13 +562,17 @@ int sq_mixer_step(sq_mixer* m, const double* v_in, const double* v_out, double* 
         Fo[i] = m->F[m->order[i]];
     }
     const double* f = Fo[k];
+    // Periodic Pulay: extrapolate on steps period-1, 2 period-1, ...; simple mixing otherwise
+    const bool pulay = (m->steps + 1) % m->period == 0;
+    m->steps++;
+    const int kd = pulay ? k : 0;                  // differences used
     // |f|^2, |v_out|^2, then dF_i . dF_j (i <= j) and dF_i . f
     int rc;
     if ((rc = enqueue_dot(m->red, f, nullptr, f, nullptr, n, 0, st)) ||
         (rc = enqueue_dot(m->red, v_out, nullptr, v_out, nullptr, n, 1, st)))
         return rc;
     int s = 2;
-    for (int i = 0; i < k; ++i) {
+    for (int i = 0; i < kd; ++i) {
         if ((rc = enqueue_dot(m->red, Fo[i + 1], Fo[i], f, nullptr, n, s++, st))) return rc;
         for (int j = 0; j <= i; ++j)
             if ((rc = enqueue_dot(m->red, Fo[i + 1], Fo[i], Fo[j + 1], Fo[j], n, s++, st))) return rc;
@@ -575,15 +581,15 @@ int sq_mixer_step(sq_mixer* m, const double* v_in, const double* v_out, double* 
     if ((rc = read_slots(m->red, h.data(), s, st))) return rc;
     if (rel_resid_host) *rel_resid_host = h[1] > 0.0 ? sqrt(h[0] / h[1]) : sqrt(h[0]);
     MixHist H = {};
-    int used = k;
-    if (k > 0) {
-        std::vector<double> Gm(k * k), cv(k);
+    int used = kd;
+    if (kd > 0) {
+        std::vector<double> Gm(kd * kd), cv(kd);
         int t = 2;
-        for (int i = 0; i < k; ++i) {
+        for (int i = 0; i < kd; ++i) {
             cv[i] = h[t++];
-            for (int j = 0; j <= i; ++j) Gm[i * k + j] = Gm[j * k + i] = h[t++];
+            for (int j = 0; j <= i; ++j) Gm[i * kd + j] = Gm[j * kd + i] = h[t++];
         }
-        if (!chol_solve(k, Gm, cv, H.g)) used = 0;   // drop the history (simple mixing)
+        if (!chol_solve(kd, Gm, cv, H.g)) used = 0;   // drop the history (simple mixing)
     }
     for (int i = 0; i <= k; ++i) {
         H.X[i] = Xo[i];
@@ -595,6 +601,14 @@ int sq_mixer_step(sq_mixer* m, const double* v_in, const double* v_out, double* 
     }
     mix_kernel<<<G, 256, 0, st>>>(H, used, m->beta, v_next, n);
     if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    return SQ_OK;
+}
+
+int sq_mixer_set_period(sq_mixer* m, int period, long long steps_done)
+{
+    if (!m || period < 1 || period > 1000 || steps_done < 0) return SQ_EINVAL;
+    m->period = period;
+    m->steps = steps_done;
     return SQ_OK;
 }
 
@@ -641,6 +655,7 @@ int sq_mixer_reset(sq_mixer* m)
 {
     if (!m) return SQ_EINVAL;
     m->order.clear();
+    m->steps = 0;
     return SQ_OK;
 }
 

@@ -25,7 +25,7 @@ EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments",
            "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
            "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
-           "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
+           "sq_mixer_set_period", "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
            "sq_nl_forces", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create", "sq_cnn_set_params", "sq_cnn_get_params",
            "sq_cnn_forward", "sq_cnn_backward", "sq_cnn_get_grads", "sq_cnn_adam_step", "sq_cnn_destroy")
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         lib.sq_poisson.argtypes = [vp, vp, vp, C.c_double, ip, C.POINTER(ip), dp]
         lib.sq_effective_potential.argtypes = [vp, vp, vp, vp, C.c_double, vp]
         lib.sq_nl_forces.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp]
+        lib.sq_mixer_set_period.argtypes = [vp, ip, C.c_longlong]
         lib.sq_kerker.argtypes = [vp, vp, vp, C.c_double, C.c_double, C.c_double, ip, vp, dp, C.POINTER(ip)]
         lib.sq_cnn_param_count.argtypes = [ip]
         lib.sq_cnn_param_count.restype = C.c_longlong
@@ -288,6 +289,10 @@ def sq_mixer_step(mixer, v_in, v_out, v_next) -> float:
     _check(load().sq_mixer_step(C.c_void_p(mixer), _dptr(v_in, "v_in"), _dptr(v_out, "v_out"),
                                 _dptr(v_next, "v_next"), C.byref(res)), "sq_mixer_step")
     return res.value
+
+
+def sq_mixer_set_period(mixer, period, steps_done=0):
+    _check(load().sq_mixer_set_period(C.c_void_p(mixer), int(period), int(steps_done)), "sq_mixer_set_period")
 
 
 def sq_mixer_export(mixer, n):

@@ -5,6 +5,11 @@ potential.
 
 Tolerance: FP64, the same arithmetic in another summation order over a
 recurrence of n_pl steps: 1e-10 of the largest force component, absolute.
+FP32 context (recurrence, D and projector sums in FP32; coefficients and
+contraction in FP64): 1e-4 of the largest component.  The rounding error of
+the FP32 recurrence grows with the degree; the same arithmetic run on the
+host gave at most 6e-6 at n_pl <= 12 and 2.3e-5 at n_pl = 260 on these
+cases, and 1e-4 leaves a factor 4.
 The spectral bounds and the Fermi level come from the oracle and are copied
 to the GPU (never the reverse), so the comparison isolates the force path.
 The whole GPU pipeline (its own bounds, moments and Fermi level) is compared
@@ -27,6 +32,7 @@ from paper_1708_07913_gb300 import SQ_FP32, SQ_FP64, SQSolver, build, sq  # noqa
 build()
 DEV = "cuda:0"
 FP64_FORCE = 1e-10
+FP32_FORCE = 1e-4
 
 
 def _dev(a):
@@ -60,19 +66,21 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("precision", [SQ_FP64, SQ_FP32])
 @pytest.mark.parametrize("name", list(CASES))
-def test_nl_forces_match_oracle(name):
+def test_nl_forces_match_oracle(name, precision):
     wl, s, pt = _system(**CASES[name])
     osys = oracle.OracleSystem(s.V, wl.h, wl.m, s.positions, pt)
     nodes = np.arange(wl.n_nodes)
     chi, zeta = osys.bounds(nodes, 40, 0.02)
     mu = float(np.median(chi))
     F_ref = osys.nl_force(nodes, chi, zeta, wl.npl, mu, wl.kT)
-    solver = SQSolver((wl.n,) * 3, wl.h, wl.r_cut, wl.npl, SQ_FP64, s.positions, pt, device=DEV)
+    solver = SQSolver((wl.n,) * 3, wl.h, wl.r_cut, wl.npl, precision, s.positions, pt, device=DEV)
     F = solver.nl_forces(_dev(s.V), mu, wl.kT, chi=_dev(chi), zeta=_dev(zeta)).cpu().numpy()
     scale = np.abs(F_ref).max()
     assert scale > 1e-4
-    np.testing.assert_allclose(F, F_ref, rtol=0, atol=FP64_FORCE * scale)
+    tol = FP64_FORCE if precision == SQ_FP64 else FP32_FORCE
+    np.testing.assert_allclose(F, F_ref, rtol=0, atol=tol * scale)
     F2 = solver.nl_forces(_dev(s.V), mu, wl.kT, chi=_dev(chi), zeta=_dev(zeta)).cpu().numpy()
     assert np.array_equal(F, F2)                                   # fixed-order sums: repeats bit for bit
     solver.close()
@@ -123,9 +131,3 @@ def test_nl_forces_arguments():
     local.bounds(V, 40, 0.02)
     assert local.nl_forces(V, 0.0, 0.1).shape == (0, 3)                        # no projectors: no force
     local.close()
-    f32 = SQSolver((wl.n,) * 3, wl.h, wl.r_cut, wl.npl, SQ_FP32, s.positions, pt, device=DEV)
-    f32.bounds(V, 40, 0.02)
-    with pytest.raises(sq.SQError) as e:
-        f32.nl_forces(V, 0.0, 0.1)
-    assert e.value.code == sq.SQ_EUNSUPPORTED
-    f32.close()

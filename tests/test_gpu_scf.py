@@ -63,10 +63,14 @@ def test_effective_potential_matches_oracle(small):
         np.testing.assert_allclose(V_out.cpu().numpy(), ref, rtol=1e-14, atol=1e-14)
 
 
-def test_mixer_matches_oracle():
+@pytest.mark.parametrize("period", [1, 3])
+def test_mixer_matches_oracle(period):
+    """Anderson mixing (period 1) and Periodic Pulay (period 3: the
+    extrapolation on steps 2, 5, 8, simple mixing on the others)."""
     rng = np.random.default_rng(9)
     n, hist, beta = 777, 4, 0.35
     mixer = sq.sq_mixer_create(n, hist, beta)
+    sq.sq_mixer_set_period(mixer, period, 0)
     Xs, Fs = [], []
     v_next = torch.empty(n, dtype=torch.float64, device=DEV)
     x = rng.standard_normal(n)
@@ -78,7 +82,8 @@ def test_mixer_matches_oracle():
         Xs.append(x.copy())
         Fs.append(f)
         Xs, Fs = Xs[-(hist + 1):], Fs[-(hist + 1):]
-        ref = oracle.anderson_step(np.array(Xs), np.array(Fs), beta)
+        use = len(Xs) if (k + 1) % period == 0 else 1
+        ref = oracle.anderson_step(np.array(Xs[-use:]), np.array(Fs[-use:]), beta)
         np.testing.assert_allclose(v_next.cpu().numpy(), ref, rtol=0, atol=1e-11 * np.abs(ref).max())
         x = v_next.cpu().numpy().copy()
     sq.sq_mixer_destroy(mixer)
