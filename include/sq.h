@@ -201,6 +201,16 @@ int sq_density_energy_noalloc(int n1, int n2, int n3, double h, int npl,
 int sq_nl_forces(sq_ctx *ctx, const double *V, const double *chi, const double *zeta,
                  double mu, double kT, double *forces);
 
+/* The same sum restricted to the nodes listed in `nodes` (device array of
+ * n_nodes int64 node indices q, 1 <= n_nodes <= N_d; a node listed twice
+ * contributes twice): the force contributions of a sample of nodes, each of
+ * which the sum over all nodes adds once.  The list is copied to the host
+ * and checked (every index in [0, N_d)) before anything is enqueued;
+ * SQ_EINVAL otherwise. */
+int sq_nl_forces_nodes(sq_ctx *ctx, const double *V, const double *chi, const double *zeta,
+                       double mu, double kT, const long long *nodes, long long n_nodes,
+                       double *forces);
+
 /* ---------------------------------------------------------------------------
  * Batch of independent systems.  The paper treats one system at a time (its
  * parallelism is over the nodes of one grid, Section 3.2); it has no

@@ -83,12 +83,17 @@ class SQSolver:
         return sq.sq_density_energy(self.ctx, self.moments, self.chi if chi is None else chi,
                                     self.zeta if zeta is None else zeta, mu, kT, self.rho)
 
-    def nl_forces(self, V, mu, kT, chi=None, zeta=None):
-        """Nonlocal atomic forces (n_atoms, 3), Ha/bohr, at Fermi level mu."""
+    def nl_forces(self, V, mu, kT, chi=None, zeta=None, nodes=None):
+        """Nonlocal atomic forces (n_atoms, 3), Ha/bohr, at Fermi level mu;
+        ``nodes`` (int64 device tensor) restricts the sum to those nodes."""
         F = self.torch.zeros(max(self.n_atoms, 1) * 3, dtype=self.torch.float64, device=self.device)
         sq.sq_set_stream(self.ctx)
-        sq.sq_nl_forces(self.ctx, V, self.chi if chi is None else chi, self.zeta if zeta is None else zeta, mu, kT,
-                        F if self.n_atoms else None)
+        chi = self.chi if chi is None else chi
+        zeta = self.zeta if zeta is None else zeta
+        if nodes is None:
+            sq.sq_nl_forces(self.ctx, V, chi, zeta, mu, kT, F if self.n_atoms else None)
+        else:
+            sq.sq_nl_forces_nodes(self.ctx, V, chi, zeta, mu, kT, nodes, F if self.n_atoms else None)
         return F[:3 * self.n_atoms].view(self.n_atoms, 3)
 
     def solve(self, V, n_electrons, kT, n_lanczos=40, margin=0.01, bounds=None):

@@ -8,6 +8,7 @@
 #include <mutex>
 #include <new>
 #include <unordered_map>
+#include <vector>
 
 #include "sq_force.cuh"
 
@@ -88,7 +89,7 @@ void ws_release(ForceWS* w)
 // recurrence precision), then the fixed-order sum over its CTAs.
 template <typename T>
 int launch_force(sq_ctx* c, const ForceLayout& L, char* base, int blocks, const double* chi, const double* zeta,
-                 double mu, double kT, double* forces)
+                 double mu, double kT, const long long* nodes, long long nq, double* forces)
 {
     ForceArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -118,6 +119,8 @@ int launch_force(sq_ctx* c, const ForceLayout& L, char* base, int blocks, const 
     a.mu = mu;
     a.kT = kT;
     a.npl = c->npl;
+    a.nodes = nodes;
+    a.nq = nq;
     // the per-CTA slices are grouped by kind: all CTAs' vectors, then all
     // candidate lists, ... (each kind contiguous, CTA b at offset b * size)
     a.vec = (T*)(base + L.vec * blocks);
@@ -152,12 +155,27 @@ void free_force_ws(sq_ctx* c)
 }
 }  // namespace sq
 
-extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta, double mu, double kT,
-                            double* forces)
+namespace {
+
+int nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta, double mu, double kT,
+              const long long* nodes, long long n_nodes, double* forces)
 {
     if (!c || !isfinite(mu) || !isfinite(kT) || kT <= 0.0) return SQ_EINVAL;
     if (!dev_ptr(V) || !dev_ptr(chi) || !dev_ptr(zeta)) return SQ_EINVAL;
     if (c->n_atoms > 0 && !dev_ptr(forces)) return SQ_EINVAL;
+    if (nodes) {
+        // the node list is checked on the host before anything is enqueued
+        if (n_nodes < 1 || n_nodes > c->g.Nd || !dev_ptr(nodes)) return SQ_EINVAL;
+        std::vector<long long> h((size_t)n_nodes);
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+            cudaMemcpy(h.data(), nodes, sizeof(long long) * n_nodes, cudaMemcpyDeviceToHost) != cudaSuccess) {
+            cudaGetLastError();
+            return SQ_ECUDA;
+        }
+        for (long long q : h)
+            if (q < 0 || q >= c->g.Nd) return SQ_EINVAL;
+    }
+    const long long nq = nodes ? n_nodes : c->g.Nd;
     if (c->n_atoms == 0) return SQ_OK;
     const int n3 = 3 * c->n_atoms;
     if (!c->has_s && !c->has_p)
@@ -166,7 +184,7 @@ extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const
     const int S = 2 * c->g.m + 1;
     const size_t tsz = c->precision == SQ_FP32 ? sizeof(float) : sizeof(double);
     const ForceLayout L = force_layout(S, c->ccap, c->n_atoms, tsz);
-    const int blocks = (int)std::min<long long>(c->g.Nd, 2LL * c->sm_count);
+    const int blocks = (int)std::min<long long>(nq, 2LL * c->sm_count);
     const size_t need = L.total * (size_t)blocks;
     ForceWS* ws = nullptr;
     {
@@ -196,8 +214,8 @@ extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const
 
     int rc = launch_build_vpad(c, V);
     if (rc) return rc;
-    rc = c->precision == SQ_FP32 ? launch_force<float>(c, L, ws->buf, blocks, chi, zeta, mu, kT, forces)
-                                 : launch_force<double>(c, L, ws->buf, blocks, chi, zeta, mu, kT, forces);
+    rc = c->precision == SQ_FP32 ? launch_force<float>(c, L, ws->buf, blocks, chi, zeta, mu, kT, nodes, nq, forces)
+                                 : launch_force<double>(c, L, ws->buf, blocks, chi, zeta, mu, kT, nodes, nq, forces);
     if (rc) return rc;
     c->launches += 2;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
@@ -209,4 +227,19 @@ extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const
         return (e & ERR_CAPACITY) ? SQ_ECAPACITY : SQ_EBOUNDS;
     }
     return SQ_OK;
+}
+
+}  // namespace
+
+extern "C" int sq_nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta, double mu, double kT,
+                            double* forces)
+{
+    return nl_forces(c, V, chi, zeta, mu, kT, nullptr, 0, forces);
+}
+
+extern "C" int sq_nl_forces_nodes(sq_ctx* c, const double* V, const double* chi, const double* zeta, double mu,
+                                  double kT, const long long* nodes, long long n_nodes, double* forces)
+{
+    if (!nodes) return SQ_EINVAL;
+    return nl_forces(c, V, chi, zeta, mu, kT, nodes, n_nodes, forces);
 }

@@ -55,6 +55,8 @@ struct ForceArgs {
     double mu;
     double kT;
     int npl;
+    const long long* nodes;          // nodes to visit (device; validated on the host), or nullptr: all
+    long long nq;                    // their number (N_d when nodes is nullptr)
     // per-CTA scratch (slices of the sizes given)
     T* vec;                          // 4 S^3 per CTA: t^{j-1}, t^j, t^{j+1}, D
     int4* cand;                      // ccap per CTA: (atom, box start relative to the region)
@@ -238,7 +240,8 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs<T> a)
     for (int i = tid; i < 3 * nl.n_atoms; i += FORCE_NT) Fc[i] = 0.0;
     const long long ctr = (long long)M + (long long)S * (M + (long long)S * M);
 
-    for (long long q = blockIdx.x; q < a.g.Nd; q += gridDim.x) {
+    for (long long iq = blockIdx.x; iq < a.nq; iq += gridDim.x) {
+        const long long q = a.nodes ? a.nodes[iq] : iq;
         const int qi = (int)(q % a.g.n1), qj = (int)((q / a.g.n1) % a.g.n2);
         const int qk = (int)(q / ((long long)a.g.n1 * a.g.n2));
         // (1) the node's projector candidates: the boxes of its tile's list

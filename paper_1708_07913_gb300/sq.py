@@ -26,7 +26,7 @@ EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
            "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
            "sq_mixer_set_period", "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
-           "sq_nl_forces", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create", "sq_cnn_set_params", "sq_cnn_get_params",
+           "sq_nl_forces", "sq_nl_forces_nodes", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create", "sq_cnn_set_params", "sq_cnn_get_params",
            "sq_cnn_forward", "sq_cnn_backward", "sq_cnn_get_grads", "sq_cnn_adam_step", "sq_cnn_destroy")
 
 
@@ -80,6 +80,7 @@ def load(path: str = LIB_PATH):
         lib.sq_poisson.argtypes = [vp, vp, vp, C.c_double, ip, C.POINTER(ip), dp]
         lib.sq_effective_potential.argtypes = [vp, vp, vp, vp, C.c_double, vp]
         lib.sq_nl_forces.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp]
+        lib.sq_nl_forces_nodes.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp, C.c_longlong, vp]
         lib.sq_mixer_set_period.argtypes = [vp, ip, C.c_longlong]
         lib.sq_kerker.argtypes = [vp, vp, vp, C.c_double, C.c_double, C.c_double, ip, vp, dp, C.POINTER(ip)]
         lib.sq_cnn_param_count.argtypes = [ip]
@@ -181,6 +182,16 @@ def sq_nl_forces(ctx, V, chi, zeta, mu, kT, forces):
     """forces: float64 CUDA tensor of n_atoms*3 (None when there are no projectors)."""
     _check(load().sq_nl_forces(C.c_void_p(ctx), _dptr(V, "V"), _dptr(chi, "chi"), _dptr(zeta, "zeta"), float(mu),
                                float(kT), _dptr(forces, "forces")), "sq_nl_forces")
+
+
+def sq_nl_forces_nodes(ctx, V, chi, zeta, mu, kT, nodes, forces):
+    """nodes: int64 CUDA tensor of node indices."""
+    import torch
+    if not (isinstance(nodes, torch.Tensor) and nodes.is_cuda and nodes.dtype == torch.int64 and nodes.is_contiguous()):
+        raise TypeError("nodes must be a contiguous int64 CUDA tensor")
+    _check(load().sq_nl_forces_nodes(C.c_void_p(ctx), _dptr(V, "V"), _dptr(chi, "chi"), _dptr(zeta, "zeta"),
+                                     float(mu), float(kT), C.c_void_p(nodes.data_ptr()), int(nodes.numel()),
+                                     _dptr(forces, "forces")), "sq_nl_forces_nodes")
 
 
 def sq_density_energy_noalloc(shape, h, npl, moments, chi, zeta, mu, kT, rho, stream=None):

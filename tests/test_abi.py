@@ -98,6 +98,7 @@ def test_calls_reject_null_context(lib):
     assert lib.sq_launch_count(None) == -1
     lib.sq_destroy(None)
     assert lib.sq_nl_forces(None, None, None, None, 0.0, 0.1, None) == sq.SQ_EINVAL
+    assert lib.sq_nl_forces_nodes(None, None, None, None, 0.0, 0.1, None, 0, None) == sq.SQ_EINVAL
 
 
 def test_cnn_host_checks(lib):

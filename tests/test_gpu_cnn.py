@@ -109,3 +109,35 @@ def test_backward_repeats_and_accumulates():
     with pytest.raises(sq.SQError):                       # no gradient yet
         sq.sq_cnn_adam_step(fresh, 1e-3)
     sq.sq_cnn_destroy(fresh)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_forward_full_size_sampled_nodes(bf16):
+    """The 64^3 grid of the warm-start target (al256_64's local potential):
+    the output at 48 seeded nodes against the oracle evaluated on the 9^3 box
+    around each node (an output depends on exactly that patch, so the box's
+    centre never sees the box's own wrap-around)."""
+    import synth
+    s = synth.make_system("al256_64")
+    V = s.V                                             # (64, 64, 64), x fastest
+    n = V.shape[0]
+    p, _, _ = _problem((4, 4, 4), seed=17)
+    p["v_shift"], p["v_scale"] = float(V.mean()), float(V.std())
+    net = sq.sq_cnn_create(32, bf16)
+    sq.sq_cnn_set_params(net, _flat(p), p["v_shift"], p["v_scale"], p["rho_scale"])
+    rho = torch.empty(V.size, dtype=torch.float64, device=DEV)
+    sq.sq_cnn_forward(net, (n, n, n), _dev(V), rho)
+    rho = rho.cpu().numpy().reshape(V.shape)
+    nodes = synth.sample_nodes(V.size, 48, seed=23)
+    ref, got = [], []
+    for q in nodes:
+        i, j, k = q % n, (q // n) % n, q // (n * n)
+        idx = [np.arange(c - 4, c + 5) % n for c in (k, j, i)]
+        patch = V[np.ix_(*idx)]
+        r, _ = cnn.forward(p, patch, bf16=bf16)
+        ref.append(r[4, 4, 4])
+        got.append(rho[k, j, i])
+    ref, got = np.array(ref), np.array(got)
+    tol = 2e-3 if bf16 else 1e-5
+    np.testing.assert_allclose(got, ref, rtol=0, atol=tol * np.abs(ref).max())
+    sq.sq_cnn_destroy(net)

@@ -86,6 +86,37 @@ def test_nl_forces_match_oracle(name, precision):
     solver.close()
 
 
+@pytest.mark.parametrize("precision", [SQ_FP64, SQ_FP32])
+def test_nl_forces_full_size_sampled_nodes(precision):
+    """al108_48 (the benchmark workload: 25^3 regions, n_pl 48, 108 atoms,
+    s + 3p), the force contributions of 16 seeded nodes on the benchmark's
+    launch configuration, against the oracle on the same nodes (the oracle's
+    bounds and Fermi level on the GPU side)."""
+    s = synth.make_system("al108_48")
+    wl = s.wl
+    nodes = synth.sample_nodes(wl.n_nodes, 16, seed=31)
+    osys = oracle.OracleSystem.from_synth(s)
+    chi, zeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
+    mu = float(np.median(chi))
+    F_ref = osys.nl_force(nodes, chi, zeta, wl.npl, mu, wl.kT)
+    solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=DEV)
+    chi_all = torch.zeros(wl.n_nodes, dtype=torch.float64, device=DEV)
+    zeta_all = torch.ones(wl.n_nodes, dtype=torch.float64, device=DEV)
+    chi_all[torch.from_numpy(nodes).to(DEV)] = _dev(chi)
+    zeta_all[torch.from_numpy(nodes).to(DEV)] = _dev(zeta)
+    F = solver.nl_forces(_dev(s.V), mu, wl.kT, chi=chi_all, zeta=zeta_all,
+                         nodes=torch.from_numpy(nodes).to(DEV)).cpu().numpy()
+    scale = np.abs(F_ref).max()
+    assert scale > 1e-5
+    tol = FP64_FORCE if precision == SQ_FP64 else FP32_FORCE
+    np.testing.assert_allclose(F, F_ref, rtol=0, atol=tol * scale)
+    with pytest.raises(sq.SQError) as e:                                    # an index outside the grid
+        bad = torch.tensor([0, wl.n_nodes], dtype=torch.int64, device=DEV)
+        solver.nl_forces(_dev(s.V), mu, wl.kT, chi=chi_all, zeta=zeta_all, nodes=bad)
+    assert e.value.code == sq.SQ_EINVAL
+    solver.close()
+
+
 def test_nl_forces_whole_pipeline():
     """GPU bounds, moments, Fermi level and forces vs the oracle's."""
     wl, s, pt = _system(**CASES["sp_n10_m3"])
