@@ -14,6 +14,7 @@ projectors, 324 electrons; synthetic, seeded inputs.
                   [--impl reference]
   python bench.py --workload batch16          (16 uneven systems as one CUDA graph)
   python bench.py --workload force_al108_48   (nonlocal atomic forces; --precision fp32|fp64)
+  python bench.py --workload scf_al256_64     (SCF to 1e-6: Kerker-preconditioned Anderson mixing)
   python bench.py --workload warmstart_c4     (train the warm-start network, then SCF
                                                iterations to 1e-6 on al256_64 with and without it)
 
@@ -63,7 +64,11 @@ def parse():
     p.add_argument("--train-geometries", type=int, default=250, help="warmstart_c4: seeded training geometries")
     p.add_argument("--train-iters", type=int, default=8, help="warmstart_c4: SCF iterations kept per geometry")
     p.add_argument("--train-steps", type=int, default=1000, help="warmstart_c4: Adam steps")
-    p.add_argument("--max-scf", type=int, default=60, help="warmstart_c4: SCF iteration limit")
+    p.add_argument("--max-scf", type=int, default=60, help="warmstart_c4, scf_*: SCF iteration limit")
+    p.add_argument("--kerker", default="0.8,0.2", help="scf_*: k0,amin of the preconditioner, or 'none'")
+    p.add_argument("--history", type=int, default=12, help="scf_*: mixing history")
+    p.add_argument("--beta", type=float, default=0.3, help="scf_*: mixing parameter")
+    p.add_argument("--period", type=int, default=1, help="scf_*: Pulay period (1: Anderson every step)")
     return p.parse_args()
 
 
@@ -652,6 +657,61 @@ def run_force(a):
     print(json.dumps(line), flush=True)
 
 
+def run_scf(a):
+    """The SCF loop (SQSCF: SQ path, CG Poisson, X-alpha, mixing) on the
+    workload named after ``scf_``, FP32 recurrence, to a 1e-6 residual.
+    Value: seconds per SCF iteration (device time of the whole loop divided
+    by its iterations)."""
+    import torch
+    from paper_1708_07913_gb300 import SQ_FP32, SQ_FP64, SQSCF, SQSolver, build
+
+    name = a.workload[len("scf_"):]
+    dev = torch.device("cuda:0")
+    torch.cuda.set_device(dev)
+    build()
+    s = synth.make_system(name)
+    wl = s.wl
+    prec = SQ_FP32 if a.precision == "fp32" else SQ_FP64
+    solver = SQSolver.from_workload(wl, s.positions, precision=prec, device=str(dev))
+    V_loc = torch.from_numpy(s.V.ravel().copy()).to(dev)
+    kerker = None if a.kerker == "none" else tuple(float(x) for x in a.kerker.split(","))
+    scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=a.beta, history=a.history, margin=wl.margin,
+                kerker=kerker, period=a.period)
+    solver.solve(V_loc, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)      # warm-up (not timed)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    launches0 = solver.launches
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    out = scf.run(tol=1e-6, max_iter=a.max_scf)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    t = e0.elapsed_time(e1) / 1e3
+    it = out["iterations"]
+    line = {
+        "metric": "seconds per SCF iteration (SQ step, Poisson, X-alpha, mixing)", "value": t / it, "unit": "s",
+        "n_gpus": 1, "steps": it, "warmup": 1, "ms_per_step": t / it * 1e3, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if prec == SQ_FP32 else "f64",
+        "data": "synthetic (seeded FCC Al-like crystal, Gaussian V and KB projectors)",
+        "config": {"workload": f"{a.workload}: {wl.cells}^3 cells ({wl.n_atoms} atoms), {wl.n}^3 grid, "
+                               f"{2 * wl.m + 1}^3 regions, n_pl={wl.npl}, kT={wl.kT}",
+                   "mixing": {"beta": a.beta, "history": a.history, "period": a.period, "kerker": kerker},
+                   "tolerance": 1e-6, "parallelism": "single GPU"},
+        "iterations": it, "converged": out["converged"], "residuals": [float(r) for r in out["residuals"]],
+        "poisson_iterations": out["poisson_iterations"], "wall_s": wall,
+        "roofline": None, "e2e": None, "cpu_baseline": None, "gpu_launches": int(solver.launches - launches0),
+        "clocks": clk,
+    }
+    scf.close()
+    solver.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(a):
     """The learned warm start on the 4x4x4-cell system (al256_64): training
     pairs from SCF iterations of seeded one-cell geometries with the same
@@ -711,6 +771,8 @@ def main():
         run_force(a)
     elif a.workload == "warmstart_c4":
         run_warmstart(a)
+    elif a.workload.startswith("scf_"):
+        run_scf(a)
     else:
         run_gb300(a)
 
