@@ -627,6 +627,8 @@ def run_force(a):
                                f"a projector support",
                    "precision": ("FP32 recurrence, D and projector sums; FP64 coefficients and contraction"
                                  if prec == SQ_FP32 else "FP64 throughout"),
+                   "vector_storage": ("global scratch (SQ_FORCE_GLOBAL=1)" if os.environ.get("SQ_FORCE_GLOBAL") == "1"
+                                      else "current vector in shared memory"),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "single GPU"},
         "forces_max_abs": float(F.abs().max().item()),

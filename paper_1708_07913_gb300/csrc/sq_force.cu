@@ -2,6 +2,7 @@
 // the per-context force workspace, and the two launches (the per-node force
 // kernel of sq_force.cuh and the fixed-order sum over its CTAs).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -87,9 +88,42 @@ void ws_release(ForceWS* w)
 
 // Arguments and launch of the force kernel in precision T (the context's
 // recurrence precision), then the fixed-order sum over its CTAs.
+// Grid and dynamic shared memory of the force kernel in precision T: the
+// in-place form keeps the current recurrence vector (S^3 values) in shared
+// memory; SQ_FORCE_GLOBAL=1 in the environment selects the form with every
+// vector in global scratch (for comparisons).  The dynamic shared-memory
+// limit of the kernel is only ever raised.
 template <typename T>
-int launch_force(sq_ctx* c, const ForceLayout& L, char* base, int blocks, const double* chi, const double* zeta,
-                 double mu, double kT, const long long* nodes, long long nq, double* forces)
+int force_config(sq_ctx* c, long long nq, bool* inplace, size_t* dyn, int* blocks)
+{
+    const int S = 2 * c->g.m + 1;
+    const char* env = getenv("SQ_FORCE_GLOBAL");
+    *inplace = !(env && env[0] == '1');
+    *dyn = *inplace ? sizeof(T) * (size_t)S * S * S : 0;
+    const void* fn = *inplace ? (const void*)nl_force_kernel<T, true> : (const void*)nl_force_kernel<T, false>;
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) {
+        cudaGetLastError();
+        return SQ_ECUDA;
+    }
+    if ((int)*dyn > fa.maxDynamicSharedSizeBytes &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*dyn) != cudaSuccess) {
+        cudaGetLastError();
+        return SQ_EUNSUPPORTED;
+    }
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, FORCE_NT, *dyn) != cudaSuccess || occ < 1) {
+        cudaGetLastError();
+        return SQ_EUNSUPPORTED;
+    }
+    *blocks = (int)std::min<long long>(nq, (long long)std::min(occ, 2) * c->sm_count);
+    return SQ_OK;
+}
+
+template <typename T>
+int launch_force(sq_ctx* c, const ForceLayout& L, char* base, int blocks, bool inplace, size_t dyn,
+                 const double* chi, const double* zeta, double mu, double kT, const long long* nodes, long long nq,
+                 double* forces)
 {
     ForceArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -134,7 +168,8 @@ int launch_force(sq_ctx* c, const ForceLayout& L, char* base, int blocks, const 
     a.part = (T*)(base + L.part * blocks);
     a.Fcta = (double*)(base + L.F * blocks);
     a.err = c->d_err;
-    nl_force_kernel<T><<<blocks, FORCE_NT, 0, c->stream>>>(a);
+    if (inplace) nl_force_kernel<T, true><<<blocks, FORCE_NT, dyn, c->stream>>>(a);
+    else nl_force_kernel<T, false><<<blocks, FORCE_NT, 0, c->stream>>>(a);
     if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
     const int n3 = 3 * c->n_atoms;
     force_sum_kernel<<<(n3 + 127) / 128, 128, 0, c->stream>>>(a.Fcta, blocks, n3, forces);
@@ -184,7 +219,12 @@ int nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta,
     const int S = 2 * c->g.m + 1;
     const size_t tsz = c->precision == SQ_FP32 ? sizeof(float) : sizeof(double);
     const ForceLayout L = force_layout(S, c->ccap, c->n_atoms, tsz);
-    const int blocks = (int)std::min<long long>(nq, 2LL * c->sm_count);
+    bool inplace = true;
+    size_t dyn = 0;
+    int blocks = 0;
+    int rcc = c->precision == SQ_FP32 ? force_config<float>(c, nq, &inplace, &dyn, &blocks)
+                                      : force_config<double>(c, nq, &inplace, &dyn, &blocks);
+    if (rcc) return rcc;
     const size_t need = L.total * (size_t)blocks;
     ForceWS* ws = nullptr;
     {
@@ -214,8 +254,9 @@ int nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta,
 
     int rc = launch_build_vpad(c, V);
     if (rc) return rc;
-    rc = c->precision == SQ_FP32 ? launch_force<float>(c, L, ws->buf, blocks, chi, zeta, mu, kT, nodes, nq, forces)
-                                 : launch_force<double>(c, L, ws->buf, blocks, chi, zeta, mu, kT, nodes, nq, forces);
+    rc = c->precision == SQ_FP32
+             ? launch_force<float>(c, L, ws->buf, blocks, inplace, dyn, chi, zeta, mu, kT, nodes, nq, forces)
+             : launch_force<double>(c, L, ws->buf, blocks, inplace, dyn, chi, zeta, mu, kT, nodes, nq, forces);
     if (rc) return rc;
     c->launches += 2;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;

@@ -106,10 +106,16 @@ struct ForceLists {
     T* P;
 };
 
-// One step y = Hhat x (xm == nullptr) or y = 2 Hhat x - xm, then D += cj y.
-template <typename T>
+// One step t' = Hhat x (first) or t' = 2 Hhat x - xm, then D += cj t'.
+//   INPLACE = false: x, xm, y in global scratch; y receives t'.
+//   INPLACE = true:  x in shared memory and overwritten by t' point by point
+//                    in phase (b) (each thread reads and writes only its own
+//                    points there); the old x goes to xm, which becomes the
+//                    next step's t^{j-1}; y holds the local part only.
+// Both forms evaluate the same expressions in the same order.
+template <typename T, bool INPLACE>
 __device__ inline void force_hhat(const ForceArgs<T>& a, int qi, int qj, int qk, int S, T chq, T zq,
-                                  const ForceLists<T>& L, const T* x, const T* xm, T* y, T* D, T cj)
+                                  const ForceLists<T>& L, T* x, T* xm, bool first, T* y, T* D, T cj)
 {
     const int tid = threadIdx.x;
     const long long S2 = (long long)S * S, S3 = S2 * S;
@@ -196,15 +202,33 @@ __device__ inline void force_hhat(const ForceArgs<T>& a, int qi, int qj, int qk,
             acc += cs * Pc[0] * (gx * gy * gz) +
                    cp * (Pc[1] * (dgx * gy * gz) + Pc[2] * (gx * dgy * gz) + Pc[3] * (gx * gy * dgz));
         }
-        T v = (acc - chq * x[p]) / zq;
-        if (xm) v = (T)2 * v - xm[p];
-        y[p] = v;
+        const T xv = x[p];
+        T v = (acc - chq * xv) / zq;
+        if (!first) v = (T)2 * v - xm[p];
+        if (INPLACE) {
+            xm[p] = xv;
+            x[p] = v;
+        } else {
+            y[p] = v;
+        }
         D[p] += cj * v;
     }
     __syncthreads();
 }
 
-template <typename T>
+// Dynamic shared memory of the force kernel (the current recurrence vector
+// in the in-place form).  A host build of this header supplies the buffer.
+#ifdef __CUDACC__
+__device__ inline unsigned char* force_dyn_smem()
+{
+    extern __shared__ __align__(16) unsigned char sq_force_dyn[];
+    return sq_force_dyn;
+}
+#else
+unsigned char* force_dyn_smem();
+#endif
+
+template <typename T, bool INPLACE>
 __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs<T> a)
 {
     __shared__ double s_fk[MAX_NPL + 1];     // Fermi function at the Chebyshev zeros
@@ -358,19 +382,30 @@ __global__ void __launch_bounds__(FORCE_NT) nl_force_kernel(ForceArgs<T> a)
         }
         __syncthreads();
         // (4) t^0 = e_q, D = c^0 t^0; the recurrence to n_pl accumulating D
-        for (long long p = tid; p < S3; p += FORCE_NT) {
-            tm[p] = p == ctr ? (T)1 : (T)0;
-            D[p] = p == ctr ? (T)s_c[0] : (T)0;
-        }
-        __syncthreads();
         const T chT = (T)chq, zT = (T)zq;
-        force_hhat<T>(a, qi, qj, qk, S, chT, zT, lists, tm, nullptr, t, D, (T)s_c[1]);
-        for (int j = 2; j <= npl; ++j) {
-            force_hhat<T>(a, qi, qj, qk, S, chT, zT, lists, t, tm, tn, D, (T)s_c[j]);
-            T* r = tm;
-            tm = t;
-            t = tn;
-            tn = r;
+        if (INPLACE) {
+            T* xs = reinterpret_cast<T*>(force_dyn_smem());
+            for (long long p = tid; p < S3; p += FORCE_NT) {
+                xs[p] = p == ctr ? (T)1 : (T)0;
+                D[p] = p == ctr ? (T)s_c[0] : (T)0;
+            }
+            __syncthreads();
+            for (int j = 1; j <= npl; ++j)
+                force_hhat<T, true>(a, qi, qj, qk, S, chT, zT, lists, xs, tm, j == 1, t, D, (T)s_c[j]);
+        } else {
+            for (long long p = tid; p < S3; p += FORCE_NT) {
+                tm[p] = p == ctr ? (T)1 : (T)0;
+                D[p] = p == ctr ? (T)s_c[0] : (T)0;
+            }
+            __syncthreads();
+            force_hhat<T, false>(a, qi, qj, qk, S, chT, zT, lists, tm, nullptr, true, t, D, (T)s_c[1]);
+            for (int j = 2; j <= npl; ++j) {
+                force_hhat<T, false>(a, qi, qj, qk, S, chT, zT, lists, t, tm, false, tn, D, (T)s_c[j]);
+                T* r = tm;
+                tm = t;
+                t = tn;
+                tn = r;
+            }
         }
         // (5) per (candidate, axis): -4 sum_comp coef chi'(q) <chi', grad_axis D>
         const long long sa[3] = {1, S, (long long)S * S};
