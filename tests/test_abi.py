@@ -99,6 +99,11 @@ def test_calls_reject_null_context(lib):
     lib.sq_destroy(None)
     assert lib.sq_nl_forces(None, None, None, None, 0.0, 0.1, None) == sq.SQ_EINVAL
     assert lib.sq_nl_forces_nodes(None, None, None, None, 0.0, 0.1, None, 0, None) == sq.SQ_EINVAL
+    res, it = C.c_double(), C.c_int()
+    assert lib.sq_kerker(None, None, None, 1.0, 0.2, 1e-10, 100, None, C.byref(res), C.byref(it)) == sq.SQ_EINVAL
+    assert lib.sq_mixer_set_period(None, 3, 0) == sq.SQ_EINVAL
+    assert lib.sq_poisson(None, None, None, 1e-10, 10, None, None) == sq.SQ_EINVAL
+    assert lib.sq_mixer_step(None, None, None, None, None) == sq.SQ_EINVAL
 
 
 def test_cnn_host_checks(lib):
