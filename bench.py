@@ -752,7 +752,8 @@ def run_warmstart(a):
         "plain_iterations": res["plain_iterations"], "plain_converged": res["plain_converged"],
         "warm_converged": res["warm_converged"], "plain_residuals": res["plain_residuals"],
         "warm_residuals": res["warm_residuals"], "surrogate_steps": res["surrogate_steps"],
-        "surrogate_residual": res["surrogate_residual"], "rho_rel_diff_plain_vs_warm": res["rho_rel_diff"],
+        "surrogate_residual": res["surrogate_residual"], "network_used": res["network_used"],
+        "rho_rel_diff_plain_vs_warm": res["rho_rel_diff"],
         "seconds": {"training_data": t_data, "training": t_train, "surrogate": res["surrogate_s"],
                     "scf_plain": res["plain_s"], "scf_warm": res["warm_s"]},
         "loss_first_last": [losses[0], losses[-1]],

@@ -308,13 +308,18 @@ class SQCNN:
 
 
 def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4, beta=0.3, history=7,
-                         poisson_tol=1e-10, kerker=None):
+                         poisson_tol=1e-10, kerker=None, accept=0.1):
     """The SCF's starting potential from the learned network: the fixed
     point of V_in -> rho = net(V_in) -> V_out = V_loc + phi[rho] + v_x(rho)
     (the SCF map with the network in place of the SQ solve, Anderson-mixed,
     Kerker-preconditioned if ``kerker`` = (k0, amin) is given, at most
     ``iters`` steps or until ||V_out - V_in|| <= tol ||V_out||).
-    Returns (V_in, residuals); every step runs in libsq."""
+    Plain SQ is the fallback: if the surrogate's last residual is not finite
+    or above ``accept``, V_loc is returned instead.  The SCF that follows
+    always runs the SQ path, which judges the result.  Returns (V_in,
+    residuals, used): ``used`` tells whether the network's potential was
+    kept.  Every step runs in libsq."""
+    import math
     torch = solver.torch
     shape = solver.shape
     f64 = dict(dtype=torch.float64, device=solver.device)
@@ -326,18 +331,23 @@ def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4
     try:
         sq.sq_set_stream(solver.ctx)
         for _ in range(iters):
-            net.predict(shape, V_in, out=rho)
-            sq.sq_poisson(solver.ctx, rho, phi, poisson_tol)
-            sq.sq_effective_potential(solver.ctx, V_loc, phi, rho, alpha, V_out)
-            if kerker is None:
-                res.append(sq.sq_mixer_step(mixer, V_in, V_out, V_next))
-            else:
-                r, _ = sq.sq_kerker(solver.ctx, V_in, V_out, kerker[0], kerker[1], V_pre)
-                sq.sq_mixer_step(mixer, V_in, V_pre, V_next)
-                res.append(r)
+            try:
+                net.predict(shape, V_in, out=rho)
+                sq.sq_poisson(solver.ctx, rho, phi, poisson_tol)
+                sq.sq_effective_potential(solver.ctx, V_loc, phi, rho, alpha, V_out)
+                if kerker is None:
+                    res.append(sq.sq_mixer_step(mixer, V_in, V_out, V_next))
+                else:
+                    r, _ = sq.sq_kerker(solver.ctx, V_in, V_out, kerker[0], kerker[1], V_pre)
+                    sq.sq_mixer_step(mixer, V_in, V_pre, V_next)
+                    res.append(r)
+            except SQError:                   # e.g. a non-finite prediction: fall back to plain SQ
+                res.append(float("nan"))
+                break
             V_in, V_next = V_next, V_in
-            if res[-1] <= tol:
+            if not math.isfinite(res[-1]) or res[-1] <= tol:   # not finite, or converged
                 break
     finally:
         sq.sq_mixer_destroy(mixer)
-    return V_in, res
+    used = bool(res) and math.isfinite(res[-1]) and res[-1] <= accept
+    return (V_in if used else V_loc.clone()), res, used

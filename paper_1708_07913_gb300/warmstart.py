@@ -83,7 +83,7 @@ def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0",
     t_plain = time.perf_counter() - t0
     rho_plain = plain["rho"].clone()
     t0 = time.perf_counter()
-    V0, surrogate = warm_start_potential(net, solver, V_loc, history=history, kerker=kerker)
+    V0, surrogate, used = warm_start_potential(net, solver, V_loc, history=history, kerker=kerker)
     t_surr = time.perf_counter() - t0
     t0 = time.perf_counter()
     warm = scf.run(V0=V0, tol=tol, max_iter=max_iter)
@@ -94,6 +94,7 @@ def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0",
                warm_iterations=warm["iterations"], warm_converged=warm["converged"],
                warm_residuals=[float(r) for r in warm["residuals"]], warm_s=t_warm,
                surrogate_steps=len(surrogate), surrogate_residual=float(surrogate[-1]), surrogate_s=t_surr,
+               network_used=used,
                rho_rel_diff=drho)
     scf.close()
     solver.close()

@@ -54,8 +54,8 @@ def test_train_then_warm_start(tmp_path):
     assert torch.equal(r1, r2)
     again.close()
 
-    V0, res = warm_start_potential(net, solver, V_loc, iters=20)
-    assert len(res) >= 1 and np.all(np.isfinite(res))
+    V0, res, used = warm_start_potential(net, solver, V_loc, iters=20)
+    assert len(res) >= 1 and np.all(np.isfinite(res)) and used
     warm = scf.run(V0=V0, tol=1e-6, max_iter=60)
     assert warm["converged"]
     np.testing.assert_allclose(warm["rho"].cpu().numpy(), rho_plain, atol=1e-5 * np.abs(rho_plain).max())
