@@ -1,0 +1,70 @@
+"""Control flow of warm_start_potential (no GPU): the libsq calls are
+replaced by stand-ins that script the surrogate's residuals, so the three
+outcomes are checked on the host: converged (the network's potential is
+kept), a rejected state (plain SQ's V_loc is returned), and a residual
+above the acceptance threshold (V_loc as well)."""
+import contextlib
+import types
+
+import pytest
+
+torch = pytest.importorskip("torch")
+
+import paper_1708_07913_gb300 as pkg  # noqa: E402
+from paper_1708_07913_gb300 import sq  # noqa: E402
+
+
+class _Net:
+    def predict(self, shape, V, out=None):
+        return out
+
+
+def _solver(n=8):
+    return types.SimpleNamespace(torch=torch, device=torch.device("cpu"), shape=(2, 2, 2), n_nodes=n, ctx=1)
+
+
+def _script(monkeypatch, residuals, fail_at=None):
+    it = {"k": 0}
+
+    def mixer_step(m, v_in, v_out, v_next):
+        v_next.copy_(v_in + 1.0)
+        r = residuals[it["k"]]
+        it["k"] += 1
+        return r
+
+    def poisson(ctx, rho, phi, tol):
+        if fail_at is not None and it["k"] == fail_at:
+            raise sq.SQError(sq.SQ_ENOCONV, "sq_poisson")
+        return 1, 0.0
+
+    monkeypatch.setattr(torch.cuda, "device", lambda d: contextlib.nullcontext())   # host tensors here
+    monkeypatch.setattr(sq, "sq_mixer_create", lambda n, h, b: 7)
+    monkeypatch.setattr(sq, "sq_mixer_destroy", lambda m: None)
+    monkeypatch.setattr(sq, "sq_set_stream", lambda ctx: None)
+    monkeypatch.setattr(sq, "sq_poisson", poisson)
+    monkeypatch.setattr(sq, "sq_effective_potential", lambda *a: None)
+    monkeypatch.setattr(sq, "sq_mixer_step", mixer_step)
+    return it
+
+
+def test_converged_surrogate_is_used(monkeypatch):
+    it = _script(monkeypatch, [0.6, 0.1, 0.01, 5e-5, 1.0])
+    V_loc = torch.zeros(8, dtype=torch.float64)
+    V, res, used = pkg.warm_start_potential(_Net(), _solver(), V_loc, iters=10, tol=1e-4)
+    assert used and res == [0.6, 0.1, 0.01, 5e-5] and it["k"] == 4
+    assert torch.all(V == 4.0)                      # four mixing steps from V_loc = 0
+
+
+def test_rejected_state_falls_back_to_plain_sq(monkeypatch):
+    _script(monkeypatch, [0.6, 0.2, 0.1], fail_at=2)
+    V_loc = torch.full((8,), 3.0, dtype=torch.float64)
+    V, res, used = pkg.warm_start_potential(_Net(), _solver(), V_loc, iters=10)
+    assert not used and len(res) == 3 and res[-1] != res[-1]      # NaN recorded
+    assert torch.equal(V, V_loc) and V.data_ptr() != V_loc.data_ptr()
+
+
+def test_unconverged_surrogate_above_threshold_falls_back(monkeypatch):
+    _script(monkeypatch, [0.6, 0.5, 0.4])
+    V_loc = torch.full((8,), -1.0, dtype=torch.float64)
+    V, res, used = pkg.warm_start_potential(_Net(), _solver(), V_loc, iters=3, accept=0.1)
+    assert not used and res == [0.6, 0.5, 0.4] and torch.equal(V, V_loc)
