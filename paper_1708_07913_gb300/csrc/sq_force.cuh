@@ -12,8 +12,10 @@
 // gradient of Eq. FD:Gradient inside the region (zero outside it).  Only
 // nodes inside the support of some projector contribute.
 //
-// One CTA per node (persistent grid).  The three recurrence vectors and D
-// live in per-CTA global scratch.  Per node, every region row (y, z) gets
+// One CTA per node (persistent grid).  The current recurrence vector lives
+// in shared memory (or, in the form kept for comparisons, in global scratch
+// with the others); t^{j-1}, the local part of H t and D are in per-CTA
+// global scratch.  Per node, every region row (y, z) gets
 // the list of candidate images whose support crosses it (x-interval and
 // box-relative row), and every candidate the list of its row entries in row
 // order.  Every step is three block-wide phases:
