@@ -24,7 +24,6 @@ int launch_build_vpad(sq_ctx* ctx, const double* V);
 struct ForceWS {
     char* buf = nullptr;
     size_t bytes = 0;
-    int blocks = 0;
 };
 
 namespace {
@@ -250,7 +249,6 @@ int nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta,
         ws->bytes = need;
         g_force_ws[c] = ws;
     }
-    ws->blocks = blocks;
 
     int rc = launch_build_vpad(c, V);
     if (rc) return rc;
