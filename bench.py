@@ -733,9 +733,9 @@ def run_warmstart(a):
     clocks = ClockSampler(0)
     clocks.start()
     pairs, t_data = wsm.training_pairs(tmpl, a.train_geometries, a.train_iters, seed=5000, device=str(dev))
-    net = SQCNN(True, 0, *wsm.input_scales(pairs), device=str(dev))
-    losses, t_train = wsm.train(net, pairs, a.train_steps)
-    res = wsm.compare(net, target, tol=1e-6, max_iter=a.max_scf, device=str(dev))
+    net = SQCNN(True, 0, *wsm.input_scales(pairs, fermi_referenced=True), device=str(dev))
+    losses, t_train = wsm.train(net, pairs, a.train_steps, fermi_referenced=True)
+    res = wsm.compare(net, target, tol=1e-6, max_iter=a.max_scf, device=str(dev), fermi_referenced=True)
     clk = clocks.stop()
     net.close()
     line = {
@@ -748,6 +748,7 @@ def run_warmstart(a):
                                "n_pl=48, kT=0.05); training on one-cell 16^3 geometries",
                    "training_pairs": len(pairs), "training_geometries": a.train_geometries,
                    "scf_iterations_per_geometry": a.train_iters, "adam_steps": a.train_steps,
+                   "network_input": "V - mu (Fermi level by bisection on the electron count at inference)",
                    "parallelism": "single GPU"},
         "plain_iterations": res["plain_iterations"], "plain_converged": res["plain_converged"],
         "warm_converged": res["warm_converged"], "plain_residuals": res["plain_residuals"],

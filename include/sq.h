@@ -366,6 +366,12 @@ void sq_mixer_destroy(sq_mixer *mx);
  *   weights (rounded to FP32), input shift/scale (v_scale != 0) and output
  *   scale (> 0); resets the Adam state.  sq_cnn_get_params: read them back.
  * sq_cnn_forward(net, n1, n2, n3, V, rho): V, rho device N FP64.
+ * sq_cnn_set_shift(net, shift): an extra constant subtracted from V before
+ *   the input scaling, x0 = (V - v_shift - shift)/v_scale, in every later
+ *   forward and backward call (0 after sq_cnn_set_params).  With shift =
+ *   the Fermi level the network maps V - mu to rho.
+ * sq_cnn_forward_sum(net, n1, n2, n3, V, rho, sum_host): the forward pass
+ *   and sum_q rho_q (HOST output; fixed-order reduction; synchronises).
  * sq_cnn_backward(net, n1, n2, n3, V, rho_ref, rho, accumulate, loss_host):
  *   forward into rho, the loss against rho_ref (all device N FP64) into
  *   loss_host (HOST, may be NULL; synchronises when given), and the
@@ -386,6 +392,9 @@ int sq_cnn_set_params(sq_cnn *net, const double *params_host, double v_shift, do
                       double rho_scale);
 int sq_cnn_get_params(sq_cnn *net, double *params_host);
 int sq_cnn_forward(sq_cnn *net, int n1, int n2, int n3, const double *V, double *rho);
+int sq_cnn_set_shift(sq_cnn *net, double shift);
+int sq_cnn_forward_sum(sq_cnn *net, int n1, int n2, int n3, const double *V, double *rho,
+                       double *sum_host);
 int sq_cnn_backward(sq_cnn *net, int n1, int n2, int n3, const double *V, const double *rho_ref,
                     double *rho, int accumulate, double *loss_host);
 int sq_cnn_get_grads(sq_cnn *net, double *grads_host);

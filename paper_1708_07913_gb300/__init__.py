@@ -184,7 +184,7 @@ class SQSCF:
         iterations per SCF step.  ``checkpoint``: a path; after every
         iteration the next input potential and the mixing history are saved
         there (.npz of .npy arrays).  ``resume``: such a file; the loop
-        continues from it (V0 is then ignored).  ``on_step(V_in, rho)`` is
+        continues from it (V0 is then ignored).  ``on_step(V_in, rho, mu)`` is
         called after every SQ solve (e.g. to collect training pairs; the
         tensors are reused by the next iteration)."""
         import numpy as np
@@ -203,7 +203,7 @@ class SQSCF:
         for it in range(len(res), max_iter):
             out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
             if on_step is not None:
-                on_step(V_in, sv.rho)
+                on_step(V_in, sv.rho, out["mu"])
             sq.sq_set_stream(sv.ctx)
             k, _ = sq.sq_poisson(sv.ctx, sv.rho, self.phi, poisson_tol)
             pit.append(k)
@@ -275,13 +275,59 @@ class SQCNN:
         return rho
 
     def train_step(self, batch, lr, beta1=0.9, beta2=0.999, eps=1e-8):
-        """One Adam step on the mean loss over ``batch`` = [(shape, V, rho_ref), ...]; returns that mean loss."""
+        """One Adam step on the mean loss over ``batch`` = [(shape, V,
+        rho_ref[, mu]), ...]; with mu the sample is seen as V - mu (the
+        Fermi-level-referenced map).  Returns that mean loss."""
         total = 0.0
-        for i, (shape, V, ref) in enumerate(batch):
+        for i, item in enumerate(batch):
+            shape, V, ref = item[:3]
+            sq.sq_cnn_set_shift(self.net, item[3] if len(item) > 3 else 0.0)
             rho = self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
             total += sq.sq_cnn_backward(self.net, shape, V, ref, rho, accumulate=i > 0)
+        sq.sq_cnn_set_shift(self.net, 0.0)
         sq.sq_cnn_adam_step(self.net, lr, beta1, beta2, eps, grad_scale=1.0 / len(batch))
         return total / len(batch)
+
+    def predict_electrons(self, shape, V, n_electrons, h, out=None, steps=50):
+        """Density of V for a network trained on V - mu: the shift mu is
+        found by bisection so that h^3 sum rho = n_electrons (the density
+        rises with mu).  Returns (rho, mu), or (None, None) when no bracket
+        is found within 20 doublings of the interval."""
+        rho = out if out is not None else self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
+        h3 = float(h) ** 3
+
+        def count(mu):
+            sq.sq_cnn_set_shift(self.net, mu)
+            return h3 * sq.sq_cnn_forward_sum(self.net, shape, V, rho)
+
+        lo, hi, width = -1.0, 1.0, 2.0
+        n_lo, n_hi = count(lo), count(hi)
+        for _ in range(20):
+            if n_lo <= n_electrons <= n_hi:
+                break
+            width *= 2.0
+            if n_lo > n_electrons:
+                lo -= width
+                n_lo = count(lo)
+            if n_hi < n_electrons:
+                hi += width
+                n_hi = count(hi)
+        else:
+            sq.sq_cnn_set_shift(self.net, 0.0)
+            return None, None
+        if not (n_lo <= n_electrons <= n_hi):
+            sq.sq_cnn_set_shift(self.net, 0.0)
+            return None, None
+        for _ in range(steps):
+            mid = 0.5 * (lo + hi)
+            if count(mid) < n_electrons:
+                lo = mid
+            else:
+                hi = mid
+        mu = 0.5 * (lo + hi)
+        count(mu)                                  # rho at the final shift
+        sq.sq_cnn_set_shift(self.net, 0.0)
+        return rho, mu
 
     def save(self, path):
         import numpy as np
@@ -308,7 +354,7 @@ class SQCNN:
 
 
 def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4, beta=0.3, history=7,
-                         poisson_tol=1e-10, kerker=None, accept=0.1):
+                         poisson_tol=1e-10, kerker=None, accept=0.1, n_electrons=None):
     """The SCF's starting potential from the learned network: the fixed
     point of V_in -> rho = net(V_in) -> V_out = V_loc + phi[rho] + v_x(rho)
     (the SCF map with the network in place of the SQ solve, Anderson-mixed,
@@ -318,7 +364,10 @@ def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4
     or above ``accept``, V_loc is returned instead.  The SCF that follows
     always runs the SQ path, which judges the result.  Returns (V_in,
     residuals, used): ``used`` tells whether the network's potential was
-    kept.  Every step runs in libsq."""
+    kept.  With ``n_electrons`` the network is the Fermi-level-referenced
+    map (trained on V - mu): each surrogate step finds mu so that the
+    predicted density holds n_electrons (SQCNN.predict_electrons).  Every
+    step runs in libsq."""
     import math
     torch = solver.torch
     shape = solver.shape
@@ -332,7 +381,11 @@ def warm_start_potential(net, solver, V_loc, alpha=2.0 / 3.0, iters=30, tol=1e-4
         sq.sq_set_stream(solver.ctx)
         for _ in range(iters):
             try:
-                net.predict(shape, V_in, out=rho)
+                if n_electrons is None:
+                    net.predict(shape, V_in, out=rho)
+                elif net.predict_electrons(shape, V_in, n_electrons, solver.h, out=rho)[0] is None:
+                    res.append(float("nan"))
+                    break
                 sq.sq_poisson(solver.ctx, rho, phi, poisson_tol)
                 sq.sq_effective_potential(solver.ctx, V_loc, phi, rho, alpha, V_out)
                 if kerker is None:

@@ -53,6 +53,7 @@ struct sq_cnn {
     cudaStream_t st = nullptr;
     int sm = 1;
     double v_shift = 0.0, v_scale = 1.0, rho_scale = 1.0;
+    double shift = 0.0;               // extra input shift (sq_cnn_set_shift)
     long long t = 0;                  // Adam steps taken
     bool have_params = false, have_grads = false;
     float *w = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
@@ -118,7 +119,7 @@ int forward_t(sq_cnn* n, const CnnGrid& g, const double* V, double* rho)
     T* a1 = (T*)n->a1;
     T* a2 = (T*)n->a2;
     const int gN = grid_for(g.N, n->sm), gNC = grid_for(g.N * C, n->sm);
-    cnn_input_kernel<T><<<gN, CNN_NT, 0, n->st>>>(g, V, n->v_shift, n->v_scale, x0);
+    cnn_input_kernel<T><<<gN, CNN_NT, 0, n->st>>>(g, V, n->v_shift + n->shift, n->v_scale, x0);
     cnn_conv_fwd_kernel<T, 1, 5><<<gNC, CNN_NT, 0, n->st>>>(g, x0, wt + OW1, n->w + OB1, n->z1, a1);
     cnn_conv_fwd_kernel<T, C, 3><<<gNC, CNN_NT, 0, n->st>>>(g, a1, wt + OW2, n->w + OB2, n->z2, a2);
     cnn_out_fwd_kernel<T><<<gN, CNN_NT, 0, n->st>>>(g, a2, wt + OW3, n->w + OB3, n->rho_scale, n->y, rho);
@@ -278,6 +279,7 @@ int sq_cnn_set_params(sq_cnn* n, const double* params_host, double v_shift, doub
     n->v_shift = v_shift;
     n->v_scale = v_scale;
     n->rho_scale = rho_scale;
+    n->shift = 0.0;
     n->t = 0;
     n->have_params = true;
     n->have_grads = false;
@@ -303,6 +305,29 @@ int sq_cnn_forward(sq_cnn* n, int n1, int n2, int n3, const double* V, double* r
     int rc = ensure(n, g.N);
     if (rc) return rc;
     return n->bf16 ? forward_t<Bf16>(n, g, V, rho) : forward_t<float>(n, g, V, rho);
+}
+
+int sq_cnn_set_shift(sq_cnn* n, double shift)
+{
+    if (!n || !std::isfinite(shift)) return SQ_EINVAL;
+    n->shift = shift;
+    return SQ_OK;
+}
+
+int sq_cnn_forward_sum(sq_cnn* n, int n1, int n2, int n3, const double* V, double* rho, double* sum_host)
+{
+    if (!sum_host) return SQ_EINVAL;
+    int rc = sq_cnn_forward(n, n1, n2, n3, V, rho);
+    if (rc) return rc;
+    CnnGrid g{n1, n2, n3, (long long)n1 * n2 * n3};
+    const int gN = std::min(grid_for(g.N, n->sm), LOSS_BLOCKS);
+    cnn_sum_kernel<<<gN, CNN_NT, 0, n->st>>>(g, rho, n->lpart);
+    cnn_loss_sum_kernel<<<1, 32, 0, n->st>>>(n->lpart, gN, 1.0, n->lout);
+    if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    if (cudaMemcpyAsync(sum_host, n->lout, sizeof(double), cudaMemcpyDeviceToHost, n->st) != cudaSuccess ||
+        cudaStreamSynchronize(n->st) != cudaSuccess)
+        return SQ_ECUDA;
+    return SQ_OK;
 }
 
 int sq_cnn_backward(sq_cnn* n, int n1, int n2, int n3, const double* V, const double* rho_ref, double* rho,

@@ -191,6 +191,23 @@ __global__ void __launch_bounds__(CNN_NT) cnn_loss_kernel(CnnGrid g, const doubl
     if (threadIdx.x == 0) part[blockIdx.x] = s[0];
 }
 
+// part[block] = sum of rho over the block's nodes (tree in shared memory).
+__global__ void __launch_bounds__(CNN_NT) cnn_sum_kernel(CnnGrid g, const double* __restrict__ rho,
+                                                         double* __restrict__ part)
+{
+    __shared__ double s[CNN_NT];
+    double acc = 0.0;
+    for (long long p = blockIdx.x * (long long)CNN_NT + threadIdx.x; p < g.N; p += (long long)gridDim.x * CNN_NT)
+        acc += rho[p];
+    s[threadIdx.x] = acc;
+    __syncthreads();
+    for (int w = CNN_NT / 2; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
 // out[0] = (sum_b part[b]) / (N rs^2), in block order (one thread).
 __global__ void cnn_loss_sum_kernel(const double* __restrict__ part, int nb, double norm, double* __restrict__ out)
 {

@@ -26,8 +26,9 @@ EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
            "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
            "sq_mixer_set_period", "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
-           "sq_nl_forces", "sq_nl_forces_nodes", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create", "sq_cnn_set_params", "sq_cnn_get_params",
-           "sq_cnn_forward", "sq_cnn_backward", "sq_cnn_get_grads", "sq_cnn_adam_step", "sq_cnn_destroy")
+           "sq_nl_forces", "sq_nl_forces_nodes", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create",
+           "sq_cnn_set_params", "sq_cnn_get_params", "sq_cnn_forward", "sq_cnn_set_shift", "sq_cnn_forward_sum",
+           "sq_cnn_backward", "sq_cnn_get_grads", "sq_cnn_adam_step", "sq_cnn_destroy")
 
 
 class SQError(RuntimeError):
@@ -89,6 +90,8 @@ def load(path: str = LIB_PATH):
         lib.sq_cnn_set_params.argtypes = [vp, dp, C.c_double, C.c_double, C.c_double]
         lib.sq_cnn_get_params.argtypes = [vp, dp]
         lib.sq_cnn_forward.argtypes = [vp, ip, ip, ip, vp, vp]
+        lib.sq_cnn_set_shift.argtypes = [vp, C.c_double]
+        lib.sq_cnn_forward_sum.argtypes = [vp, ip, ip, ip, vp, vp, dp]
         lib.sq_cnn_backward.argtypes = [vp, ip, ip, ip, vp, vp, vp, ip, dp]
         lib.sq_cnn_get_grads.argtypes = [vp, dp]
         lib.sq_cnn_adam_step.argtypes = [vp, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]
@@ -364,6 +367,18 @@ def sq_cnn_forward(net, shape, V, rho):
     n1, n2, n3 = shape
     _check(load().sq_cnn_forward(C.c_void_p(net), int(n1), int(n2), int(n3), _dptr(V, "V"), _dptr(rho, "rho")),
            "sq_cnn_forward")
+
+
+def sq_cnn_set_shift(net, shift):
+    _check(load().sq_cnn_set_shift(C.c_void_p(net), float(shift)), "sq_cnn_set_shift")
+
+
+def sq_cnn_forward_sum(net, shape, V, rho) -> float:
+    n1, n2, n3 = shape
+    tot = C.c_double()
+    _check(load().sq_cnn_forward_sum(C.c_void_p(net), int(n1), int(n2), int(n3), _dptr(V, "V"), _dptr(rho, "rho"),
+                                     C.byref(tot)), "sq_cnn_forward_sum")
+    return tot.value
 
 
 def sq_cnn_backward(net, shape, V, rho_ref, rho, accumulate=False, want_loss=True):

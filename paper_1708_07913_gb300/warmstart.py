@@ -24,9 +24,10 @@ from . import SQ_FP32, SQCNN, SQSCF, SQSolver, warm_start_potential
 
 
 def training_pairs(template, n_geometries, iters, seed, precision=SQ_FP32, device="cuda:0"):
-    """(shape, V_in, rho) device pairs from ``iters`` SCF iterations on each
-    of ``n_geometries`` geometries of ``template`` (a synth.Workload), seeds
-    seed, seed + 1, ...  Returns (pairs, seconds)."""
+    """(shape, V_in, rho, mu) device pairs (mu: the SQ Fermi level of that
+    solve) from ``iters`` SCF iterations on each of ``n_geometries``
+    geometries of ``template`` (a synth.Workload), seeds seed, seed + 1, ...
+    Returns (pairs, seconds)."""
     import torch
     pairs = []
     t0 = time.perf_counter()
@@ -37,24 +38,28 @@ def training_pairs(template, n_geometries, iters, seed, precision=SQ_FP32, devic
         V_loc = torch.from_numpy(s.V.ravel().copy()).to(device)
         scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, margin=wl.margin)
         shape = (wl.n,) * 3
-        scf.run(tol=0.0, max_iter=iters, on_step=lambda V, rho: pairs.append((shape, V.clone(), rho.clone())))
+        scf.run(tol=0.0, max_iter=iters,
+                on_step=lambda V, rho, mu: pairs.append((shape, V.clone(), rho.clone(), float(mu))))
         scf.close()
         solver.close()
     torch.cuda.synchronize()
     return pairs, time.perf_counter() - t0
 
 
-def input_scales(pairs):
+def input_scales(pairs, fermi_referenced=True):
     """(v_shift, v_scale, rho_scale) from the training pairs: mean and
-    standard deviation of V, mean of rho (host reductions of copies)."""
-    V = np.concatenate([p[1].cpu().numpy() for p in pairs[: min(len(pairs), 64)]])
-    rho = np.concatenate([p[2].cpu().numpy() for p in pairs[: min(len(pairs), 64)]])
+    standard deviation of the network's input (V - mu, or V), mean of rho
+    (host reductions of copies)."""
+    some = pairs[: min(len(pairs), 64)]
+    V = np.concatenate([p[1].cpu().numpy() - (p[3] if fermi_referenced else 0.0) for p in some])
+    rho = np.concatenate([p[2].cpu().numpy() for p in some])
     return float(V.mean()), float(V.std()), float(rho.mean())
 
 
-def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=0):
+def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=0, fermi_referenced=True):
     """Adam on random minibatches, learning rate decayed geometrically from
-    lr to lr_final.  Returns (losses, seconds)."""
+    lr to lr_final; with ``fermi_referenced`` the network learns V - mu -> rho.
+    Returns (losses, seconds)."""
     import torch
     rng = np.random.default_rng(seed)
     losses = []
@@ -62,7 +67,7 @@ def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=
     for k in range(steps):
         r = lr * (lr_final / lr) ** (k / max(1, steps - 1))
         idx = rng.choice(len(pairs), size=min(batch, len(pairs)), replace=False)
-        losses.append(net.train_step([pairs[i] for i in idx], r))
+        losses.append(net.train_step([pairs[i] if fermi_referenced else pairs[i][:3] for i in idx], r))
         if log_every and k % log_every == 0:
             print(f"step {k} loss {losses[-1]:.4e}", flush=True)
     torch.cuda.synchronize()
@@ -70,7 +75,7 @@ def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=
 
 
 def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=12,
-            kerker=(0.8, 0.2)):
+            kerker=(0.8, 0.2), fermi_referenced=True):
     """SCF iterations of ``wl`` from V_loc and from the warm start (the same
     mixer, Kerker-preconditioned unless ``kerker`` is None)."""
     import torch
@@ -83,7 +88,8 @@ def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0",
     t_plain = time.perf_counter() - t0
     rho_plain = plain["rho"].clone()
     t0 = time.perf_counter()
-    V0, surrogate, used = warm_start_potential(net, solver, V_loc, history=history, kerker=kerker)
+    V0, surrogate, used = warm_start_potential(net, solver, V_loc, history=history, kerker=kerker,
+                                               n_electrons=wl.n_electrons if fermi_referenced else None)
     t_surr = time.perf_counter() - t0
     t0 = time.perf_counter()
     warm = scf.run(V0=V0, tol=tol, max_iter=max_iter)

@@ -33,17 +33,18 @@ def test_train_then_warm_start(tmp_path):
     shape = (wl.n,) * 3
     pairs = []
     scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT)
-    plain = scf.run(tol=1e-6, max_iter=60, on_step=lambda V, rho: pairs.append((shape, V.clone(), rho.clone())))
+    plain = scf.run(tol=1e-6, max_iter=60,
+                    on_step=lambda V, rho, mu: pairs.append((shape, V.clone(), rho.clone(), float(mu))))
     assert plain["converged"] and len(pairs) == plain["iterations"]
     rho_plain = plain["rho"].cpu().numpy().copy()
 
     net = SQCNN(bf16=True, seed=3, v_shift=float(s.V.mean()), v_scale=float(s.V.std()),
                 rho_scale=float(pairs[-1][2].mean().item()))
-    first = net.train_step(pairs[:3], lr=3e-3)
+    first = net.train_step([p[:3] for p in pairs[:3]], lr=3e-3)
     rng = np.random.default_rng(0)
     for _ in range(60):
         idx = rng.choice(len(pairs), size=min(3, len(pairs)), replace=False)
-        last = net.train_step([pairs[i] for i in idx], lr=3e-3)
+        last = net.train_step([pairs[i][:3] for i in idx], lr=3e-3)
     assert np.isfinite(last) and last < 0.5 * first
 
     path = str(tmp_path / "net.npz")
@@ -60,6 +61,48 @@ def test_train_then_warm_start(tmp_path):
     assert warm["converged"]
     np.testing.assert_allclose(warm["rho"].cpu().numpy(), rho_plain, atol=1e-5 * np.abs(rho_plain).max())
     print(f"SCF iterations: plain {plain['iterations']}, warm start {warm['iterations']}")
+    net.close()
+    scf.close()
+    solver.close()
+
+
+def test_fermi_referenced_warm_start():
+    """The network trained on V - mu; each surrogate step finds mu so that
+    the predicted density holds N_e electrons; the SCF from that start
+    reaches the same fixed point."""
+    wl = synth.custom_workload("ws8m", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1751)
+    s = synth.make_system(wl)
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    V_loc = _dev(s.V)
+    shape = (wl.n,) * 3
+    pairs = []
+    scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT)
+    plain = scf.run(tol=1e-6, max_iter=60,
+                    on_step=lambda V, rho, mu: pairs.append((shape, V.clone(), rho.clone(), float(mu))))
+    rho_plain = plain["rho"].cpu().numpy().copy()
+    mus = np.array([p[3] for p in pairs])
+    Vm = np.concatenate([p[1].cpu().numpy() - p[3] for p in pairs])
+    net = SQCNN(bf16=True, seed=4, v_shift=float(Vm.mean()), v_scale=float(Vm.std()),
+                rho_scale=float(pairs[-1][2].mean().item()))
+    first = net.train_step(pairs[:3], lr=3e-3)
+    rng = np.random.default_rng(1)
+    for _ in range(60):
+        idx = rng.choice(len(pairs), size=min(3, len(pairs)), replace=False)
+        last = net.train_step([pairs[i] for i in idx], lr=3e-3)
+    assert np.isfinite(last) and last < 0.5 * first
+    rho, mu = net.predict_electrons(shape, pairs[-1][1], wl.n_electrons, wl.h)
+    assert rho is not None and mus.min() - 1.0 < mu < mus.max() + 1.0
+    # bfloat16 storage rounds the shifted input, so N(mu) is a fine staircase: the
+    # bisection lands on a step, within one step of N_e
+    assert abs(wl.h ** 3 * rho.sum().item() - wl.n_electrons) < 1e-3 * wl.n_electrons
+    V0, res, used = warm_start_potential(net, solver, V_loc, iters=20, n_electrons=wl.n_electrons)
+    assert np.all(np.isfinite(res))
+    warm = scf.run(V0=V0, tol=1e-6, max_iter=60)
+    assert warm["converged"]
+    np.testing.assert_allclose(warm["rho"].cpu().numpy(), rho_plain, atol=1e-5 * np.abs(rho_plain).max())
+    print(f"SCF iterations: plain {plain['iterations']}, Fermi-referenced warm start {warm['iterations']} "
+          f"(network used: {used})")
     net.close()
     scf.close()
     solver.close()

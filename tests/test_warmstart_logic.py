@@ -68,3 +68,22 @@ def test_unconverged_surrogate_above_threshold_falls_back(monkeypatch):
     V_loc = torch.full((8,), -1.0, dtype=torch.float64)
     V, res, used = pkg.warm_start_potential(_Net(), _solver(), V_loc, iters=3, accept=0.1)
     assert not used and res == [0.6, 0.5, 0.4] and torch.equal(V, V_loc)
+
+
+def test_predict_electrons_bisects_the_shift(monkeypatch):
+    """SQCNN.predict_electrons with a scripted count N(mu) = 10 + 4 tanh(mu - 0.3)
+    (per h^3): the shift found puts N_e electrons in the density; a count that
+    never reaches N_e gives (None, None)."""
+    import math
+    state = {"mu": 0.0}
+    monkeypatch.setattr(sq, "sq_cnn_set_shift", lambda net, mu: state.__setitem__("mu", mu))
+    monkeypatch.setattr(sq, "sq_cnn_forward_sum", lambda net, shape, V, rho: 10.0 + 4.0 * math.tanh(state["mu"] - 0.3))
+    monkeypatch.setattr(sq, "sq_cnn_destroy", lambda net: None)        # the handle below is a stand-in
+    net = pkg.SQCNN.__new__(pkg.SQCNN)
+    net.torch, net.device, net.net = torch, torch.device("cpu"), 1
+    V = torch.zeros(8, dtype=torch.float64)
+    rho, mu = net.predict_electrons((2, 2, 2), V, n_electrons=12.0, h=1.0)
+    assert abs(mu - (0.3 + math.atanh(0.5))) < 1e-12 and state["mu"] == 0.0     # shift reset afterwards
+    rho, mu = net.predict_electrons((2, 2, 2), V, n_electrons=20.0, h=1.0)     # unreachable: 10 + 4 tanh < 14
+    assert rho is None and mu is None
+    net.net = None
