@@ -141,3 +141,22 @@ def test_forward_full_size_sampled_nodes(bf16):
     tol = 2e-3 if bf16 else 1e-5
     np.testing.assert_allclose(got, ref, rtol=0, atol=tol * np.abs(ref).max())
     sq.sq_cnn_destroy(net)
+
+
+@pytest.mark.parametrize("bf16", [False, True])
+def test_input_shift_and_density_sum(bf16):
+    """sq_cnn_set_shift(s) makes the network see V - s; sq_cnn_forward_sum
+    returns sum rho.  Against the oracle on V - s."""
+    shape = (9, 8, 10)
+    p, V, _ = _problem(shape, seed=41)
+    net = sq.sq_cnn_create(32, bf16)
+    sq.sq_cnn_set_params(net, _flat(p), p["v_shift"], p["v_scale"], p["rho_scale"])
+    rho = torch.empty(V.size, dtype=torch.float64, device=DEV)
+    for s in (0.0, 0.37, -1.25):
+        sq.sq_cnn_set_shift(net, s)
+        tot = sq.sq_cnn_forward_sum(net, shape, _dev(V), rho)
+        ref, _ = cnn.forward(p, V - s, bf16=bf16)
+        tol = 2e-3 if bf16 else 1e-5
+        np.testing.assert_allclose(rho.cpu().numpy(), ref.ravel(), rtol=0, atol=tol * np.abs(ref).max())
+        assert abs(tot - rho.cpu().numpy().sum()) <= 1e-12 * abs(tot)
+    sq.sq_cnn_destroy(net)
