@@ -717,9 +717,11 @@ def run_scf(a):
 def run_warmstart(a):
     """The learned warm start on the 4x4x4-cell system (al256_64): training
     pairs from SCF iterations of seeded one-cell geometries with the same
-    grid spacing, region, degree and temperature; training of the network
-    with its own kernels; then the SCF of al256_64 to 1e-6 from V_loc and
-    from the warm start.  Value: SCF iterations with the warm start."""
+    grid spacing, region, degree and temperature; two networks trained on
+    them with their own kernels (input V, and input V - mu with mu fixed by
+    the electron count at inference); then the SCF of al256_64 to 1e-6 from
+    V_loc and from each warm start.  Value: SCF iterations with the better
+    warm start."""
     import torch
     from paper_1708_07913_gb300 import SQCNN, build
     from paper_1708_07913_gb300 import warmstart as wsm
@@ -733,31 +735,32 @@ def run_warmstart(a):
     clocks = ClockSampler(0)
     clocks.start()
     pairs, t_data = wsm.training_pairs(tmpl, a.train_geometries, a.train_iters, seed=5000, device=str(dev))
-    net = SQCNN(True, 0, *wsm.input_scales(pairs, fermi_referenced=True), device=str(dev))
-    losses, t_train = wsm.train(net, pairs, a.train_steps, fermi_referenced=True)
-    res = wsm.compare(net, target, tol=1e-6, max_iter=a.max_scf, device=str(dev), fermi_referenced=True)
+    nets, t_train, losses = {}, {}, {}
+    for label, fermi in (("warm_V", False), ("warm_V_minus_mu", True)):
+        net = SQCNN(True, 0, *wsm.input_scales(pairs, fermi_referenced=fermi), device=str(dev))
+        losses[label], t_train[label] = wsm.train(net, pairs, a.train_steps, fermi_referenced=fermi)
+        nets[label] = (net, fermi)
+    res = wsm.compare(nets, target, tol=1e-6, max_iter=a.max_scf, device=str(dev))
     clk = clocks.stop()
-    net.close()
+    for net, _ in nets.values():
+        net.close()
+    best = min(("warm_V", "warm_V_minus_mu"), key=lambda k: (not res[k]["converged"], res[k]["iterations"]))
     line = {
         "metric": "SCF iterations to a 1e-6 residual (al256_64) with the learned warm start",
-        "value": res["warm_iterations"], "unit": "iterations", "n_gpus": 1, "steps": 1, "warmup": 0,
-        "ms_per_step": res["warm_s"] * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "value": res[best]["iterations"], "unit": "iterations", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": res[best]["seconds"] * 1e3, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "bf16 network (FP32 accumulation), FP32 SQ recurrence with FP64 moments",
         "data": "synthetic (seeded FCC Al-like crystals, Gaussian V and KB projectors)",
         "config": {"workload": "warmstart_c4: target al256_64 (4^3 cells, 256 atoms, 64^3 grid, 25^3 regions, "
                                "n_pl=48, kT=0.05); training on one-cell 16^3 geometries",
                    "training_pairs": len(pairs), "training_geometries": a.train_geometries,
                    "scf_iterations_per_geometry": a.train_iters, "adam_steps": a.train_steps,
-                   "network_input": "V - mu (Fermi level by bisection on the electron count at inference)",
+                   "mixing": "Anderson, history 12, beta 0.3, Kerker (0.8, 0.2)", "best": best,
                    "parallelism": "single GPU"},
-        "plain_iterations": res["plain_iterations"], "plain_converged": res["plain_converged"],
-        "warm_converged": res["warm_converged"], "plain_residuals": res["plain_residuals"],
-        "warm_residuals": res["warm_residuals"], "surrogate_steps": res["surrogate_steps"],
-        "surrogate_residual": res["surrogate_residual"], "network_used": res["network_used"],
-        "rho_rel_diff_plain_vs_warm": res["rho_rel_diff"],
-        "seconds": {"training_data": t_data, "training": t_train, "surrogate": res["surrogate_s"],
-                    "scf_plain": res["plain_s"], "scf_warm": res["warm_s"]},
-        "loss_first_last": [losses[0], losses[-1]],
+        "plain_iterations": res["plain"]["iterations"], "plain_converged": res["plain"]["converged"],
+        "results": res,
+        "seconds": {"training_data": t_data, "training": t_train},
+        "loss_first_last": {k: [v[0], v[-1]] for k, v in losses.items()},
         "roofline": None, "e2e": None, "cpu_baseline": None, "gpu_launches": None, "clocks": clk,
     }
     print(json.dumps(line), flush=True)

@@ -74,10 +74,15 @@ def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=
     return losses, time.perf_counter() - t0
 
 
-def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=12,
-            kerker=(0.8, 0.2), fermi_referenced=True):
-    """SCF iterations of ``wl`` from V_loc and from the warm start (the same
-    mixer, Kerker-preconditioned unless ``kerker`` is None)."""
+def compare(nets, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=12,
+            kerker=(0.8, 0.2)):
+    """SCF iterations of ``wl`` from V_loc and from the warm start of each
+    network in ``nets`` = {label: (net, fermi_referenced)}, all with the same
+    mixer (Kerker-preconditioned unless ``kerker`` is None).  Returns
+    {"plain": {...}, label: {...}} with iterations, convergence, residual
+    histories, times, and for the warm starts the surrogate's steps and
+    residual, whether the network's potential was kept, and the largest
+    density difference to the plain SCF's fixed point."""
     import torch
     s = synth.make_system(wl)
     solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=device)
@@ -85,23 +90,21 @@ def compare(net, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0",
     scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=beta, history=history, margin=wl.margin, kerker=kerker)
     t0 = time.perf_counter()
     plain = scf.run(tol=tol, max_iter=max_iter)
-    t_plain = time.perf_counter() - t0
+    out = {"plain": dict(iterations=plain["iterations"], converged=plain["converged"],
+                         residuals=[float(r) for r in plain["residuals"]], seconds=time.perf_counter() - t0)}
     rho_plain = plain["rho"].clone()
-    t0 = time.perf_counter()
-    V0, surrogate, used = warm_start_potential(net, solver, V_loc, history=history, kerker=kerker,
-                                               n_electrons=wl.n_electrons if fermi_referenced else None)
-    t_surr = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    warm = scf.run(V0=V0, tol=tol, max_iter=max_iter)
-    t_warm = time.perf_counter() - t0
-    drho = float((warm["rho"] - rho_plain).abs().max().item() / rho_plain.abs().max().item())
-    out = dict(plain_iterations=plain["iterations"], plain_converged=plain["converged"],
-               plain_residuals=[float(r) for r in plain["residuals"]], plain_s=t_plain,
-               warm_iterations=warm["iterations"], warm_converged=warm["converged"],
-               warm_residuals=[float(r) for r in warm["residuals"]], warm_s=t_warm,
-               surrogate_steps=len(surrogate), surrogate_residual=float(surrogate[-1]), surrogate_s=t_surr,
-               network_used=used,
-               rho_rel_diff=drho)
+    for label, (net, fermi) in nets.items():
+        t0 = time.perf_counter()
+        V0, surrogate, used = warm_start_potential(net, solver, V_loc, history=history, kerker=kerker,
+                                                   n_electrons=wl.n_electrons if fermi else None)
+        t_surr = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        warm = scf.run(V0=V0, tol=tol, max_iter=max_iter)
+        drho = float((warm["rho"] - rho_plain).abs().max().item() / rho_plain.abs().max().item())
+        out[label] = dict(iterations=warm["iterations"], converged=warm["converged"],
+                          residuals=[float(r) for r in warm["residuals"]], seconds=time.perf_counter() - t0,
+                          surrogate_steps=len(surrogate), surrogate_residual=float(surrogate[-1]),
+                          surrogate_seconds=t_surr, network_used=used, rho_rel_diff=drho)
     scf.close()
     solver.close()
     return out
