@@ -11,6 +11,16 @@
  * boundary), the Fermi level mu that puts N_e electrons in the cell, and the
  * nodal electron density, band-structure energy and electronic entropy.
  *
+ * Entry points, by group
+ *   - the path: sq_setup_grid, sq_spectral_bounds, sq_moments,
+ *     sq_fermi_level, sq_density_energy (+ sq_density_energy_noalloc);
+ *   - forces: sq_nl_forces, sq_nl_forces_nodes (Section 3.4);
+ *   - batched systems: sq_batch_* (one CUDA graph per step);
+ *   - SCF loop: sq_poisson, sq_effective_potential, sq_kerker, sq_mixer_*;
+ *   - learned SCF warm start: sq_cnn_*;
+ *   - housekeeping: sq_set_stream, sq_sync, sq_launch_count, sq_destroy,
+ *     sq_strerror.
+ *
  * Conventions
  *   - Hartree atomic units (Ha, bohr).
  *   - Grid: n1 x n2 x n3 nodes, spacing h, node (i,j,k) at (i h, j h, k h);
