@@ -72,6 +72,7 @@ def _load():
             lib.or_density_energy.argtypes = [C.c_long, C.c_int, dp, dp, dp, C.c_double, C.c_double,
                                               C.c_double, dp, dp, dp, dp]
             lib.or_nl_force.argtypes = [sp, C.c_long, lp, dp, dp, C.c_int, C.c_double, C.c_double, dp]
+            lib.or_grad_weights.argtypes = [C.c_int, C.c_double, dp]
             lib.or_laplacian_periodic.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp]
             lib.or_poisson_cg.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_int, dp, dp, C.c_double,
                                           C.c_int, ip, dp]
@@ -90,6 +91,14 @@ def _dp(a):
 
 def _f64(a):
     return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def grad_weights(no: int, h: float) -> np.ndarray:
+    """Central first-derivative weights of Eq. (FD:Gradient), index d = 0..no (wt[0] = 0)."""
+    wt = np.zeros(no + 1)
+    if _load().or_grad_weights(int(no), float(h), _dp(wt)) != 0:
+        raise ValueError("bad FD parameters")
+    return wt
 
 
 def fd_weights(no: int, h: float) -> np.ndarray:

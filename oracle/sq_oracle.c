@@ -640,16 +640,27 @@ static void grad_apply(const or_op *op, const double *wt, int axis, const double
             }
 }
 
+/* Eq. (FD:Gradient): central first-derivative weights
+ *   wt_d = (-1)^{d+1} (n_o!)^2 / (h d (n_o-d)! (n_o+d)!),  d = 1..n_o,
+ * so that f'(x) ~ sum_d wt_d (f(x + d h) - f(x - d h)); wt[0] = 0. */
+int or_grad_weights(int no, double h, double *wt)
+{
+    if (no < 1 || no > OR_MAX_NO || !(h > 0.0)) return 1;
+    wt[0] = 0.0;
+    for (int d = 1; d <= no; ++d) {
+        double sign = (d % 2 == 1) ? 1.0 : -1.0;             /* (-1)^{d+1} */
+        wt[d] = sign / (h * d) * factorial(no) * factorial(no) / (factorial(no - d) * factorial(no + d));
+    }
+    return 0;
+}
+
 int or_nl_force(const or_sys *s, long nq, const long *nodes, const double *chi, const double *zeta, int npl,
                 double mu, double kT, double *F)
 {
     if (npl < 1 || !(kT > 0.0)) return 1;
     const int no = s->no;
     double wt[OR_MAX_NO + 1];
-    for (int d = 1; d <= no; ++d) {
-        double sign = (d % 2 == 1) ? 1.0 : -1.0;             /* (-1)^{d+1} */
-        wt[d] = sign / (s->h * d) * factorial(no) * factorial(no) / (factorial(no - d) * factorial(no + d));
-    }
+    if (or_grad_weights(no, s->h, wt)) return 1;
     const double h3 = s->h * s->h * s->h;
     double *c = (double *)malloc(sizeof(double) * (npl + 1));
     for (long iq = 0; iq < nq; ++iq) {

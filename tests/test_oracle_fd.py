@@ -81,3 +81,31 @@ def test_3d_kinetic_exact_on_polynomial():
     np.testing.assert_allclose(y[inner], -0.5 * lap[inner], rtol=0, atol=1e-9 * np.abs(f).max() / h ** 2)
     # at the faces the stencil is truncated (zero Dirichlet): not equal there
     assert np.abs(y[0] - (-0.5 * lap[0])).max() > 1e-3
+
+
+@pytest.mark.parametrize("no", [1, 2, 4, 6])
+def test_gradient_weights_exact_on_polynomials(no):
+    """The central difference of order 2 n_o (Eq. FD:Gradient) differentiates
+    every polynomial of degree <= 2 n_o exactly, and misses x^(2 n_o + 1)."""
+    h, x0 = 0.37, 0.8
+    wt = oracle.grad_weights(no, h)
+    assert wt[0] == 0.0
+    for k in range(2 * no + 2):
+        f = lambda x: x ** k
+        approx = sum(wt[d] * (f(x0 + d * h) - f(x0 - d * h)) for d in range(1, no + 1))
+        exact = k * x0 ** (k - 1) if k else 0.0
+        if k <= 2 * no:
+            assert abs(approx - exact) <= 1e-10 * max(1.0, abs(exact))
+        else:
+            assert abs(approx - exact) > 1e-8
+
+
+def test_gradient_weights_converge_at_order_2no():
+    """On sin(x) the error falls as h^(2 n_o): halving h divides it by ~2^12 for n_o = 6."""
+    x0 = 0.3
+    errs = []
+    for h in (0.4, 0.2):
+        wt = oracle.grad_weights(6, h)
+        approx = sum(wt[d] * (np.sin(x0 + d * h) - np.sin(x0 - d * h)) for d in range(1, 7))
+        errs.append(abs(approx - np.cos(x0)))
+    assert 2 ** 11 < errs[0] / errs[1] < 2 ** 13
