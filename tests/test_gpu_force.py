@@ -86,15 +86,18 @@ def test_nl_forces_match_oracle(name, precision):
     solver.close()
 
 
-@pytest.mark.parametrize("precision", [SQ_FP64, SQ_FP32])
-def test_nl_forces_full_size_sampled_nodes(precision):
-    """al108_48 (the benchmark workload: 25^3 regions, n_pl 48, 108 atoms,
-    s + 3p), the force contributions of 16 seeded nodes on the benchmark's
-    launch configuration, against the oracle on the same nodes (the oracle's
-    bounds and Fermi level on the GPU side)."""
-    s = synth.make_system("al108_48")
+@pytest.mark.parametrize("name,precision,count", [("al108_48", SQ_FP64, 16), ("al108_48", SQ_FP32, 16),
+                                                  ("al2048_128", SQ_FP32, 6)])
+def test_nl_forces_full_size_sampled_nodes(name, precision, count):
+    """Full-size workloads: al108_48 (the benchmark workload: 25^3 regions,
+    n_pl 48, 108 atoms) and al2048_128 (the scale workload: 128^3 grid, 29^3
+    regions, n_pl 64, 2048 atoms; FP32, as FP64 regions stop at 25^3), s + 3p.
+    The force contributions of seeded nodes on the benchmark's launch
+    configuration, against the oracle on the same nodes (the oracle's bounds
+    and Fermi level on the GPU side)."""
+    s = synth.make_system(name)
     wl = s.wl
-    nodes = synth.sample_nodes(wl.n_nodes, 16, seed=31)
+    nodes = synth.sample_nodes(wl.n_nodes, count, seed=31)
     osys = oracle.OracleSystem.from_synth(s)
     chi, zeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
     mu = float(np.median(chi))
