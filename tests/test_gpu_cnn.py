@@ -160,3 +160,38 @@ def test_input_shift_and_density_sum(bf16):
         np.testing.assert_allclose(rho.cpu().numpy(), ref.ravel(), rtol=0, atol=tol * np.abs(ref).max())
         assert abs(tot - rho.cpu().numpy().sum()) <= 1e-12 * abs(tot)
     sq.sq_cnn_destroy(net)
+
+
+def test_full_size_gradient_is_the_derivative_of_the_loss():
+    """At 64^3 (the warm-start target's grid; FP32 storage, so the loss is
+    smooth in the weights) the stored gradient is the derivative of the
+    device's own loss: g . (theta+ - theta-) equals L(theta+) - L(theta-)
+    for theta +- eps d along a seeded direction, to the FD truncation and
+    FP32 rounding (1e-2 relative)."""
+    import synth
+    s = synth.make_system("al256_64")
+    V = s.V
+    n = V.shape[0]
+    p, _, _ = _problem((4, 4, 4), seed=29)
+    p["v_shift"], p["v_scale"] = float(V.mean()), float(V.std())
+    rng = np.random.default_rng(30)
+    ref = _dev(rng.uniform(0.0, 0.06, size=V.size))
+    Vd = _dev(V)
+    rho = torch.empty(V.size, dtype=torch.float64, device=DEV)
+    net = sq.sq_cnn_create(32, False)
+    theta = _flat(p)
+    sq.sq_cnn_set_params(net, theta, p["v_shift"], p["v_scale"], p["rho_scale"])
+    sq.sq_cnn_backward(net, (n, n, n), Vd, ref, rho)
+    g = sq.sq_cnn_get_grads(net)
+    d = rng.standard_normal(theta.size)
+    d /= np.linalg.norm(d)
+    eps = 2e-3 * np.linalg.norm(theta)
+    losses, thetas = [], []
+    for sgn in (1.0, -1.0):
+        sq.sq_cnn_set_params(net, theta + sgn * eps * d, p["v_shift"], p["v_scale"], p["rho_scale"])
+        thetas.append(sq.sq_cnn_get_params(net))                 # as rounded to FP32
+        losses.append(sq.sq_cnn_backward(net, (n, n, n), Vd, ref, rho))
+    fd = losses[0] - losses[1]
+    an = float(g @ (thetas[0] - thetas[1]))
+    assert abs(fd) > 1e-6 and abs(an - fd) <= 1e-2 * abs(fd)
+    sq.sq_cnn_destroy(net)
