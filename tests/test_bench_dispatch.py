@@ -26,3 +26,22 @@ def test_dispatch(monkeypatch, argv, runner):
     bench.main()
     name, a = called["name"]
     assert name == runner and a.warmup == 3
+
+
+def test_reference_arm_json_line(monkeypatch, capsys):
+    """The oracle arm on a small sample of al4_16 prints one JSON line with
+    the base contract's keys, the oracle described as its CPU baseline and
+    an e2e entry with no host-device bytes."""
+    import json
+    monkeypatch.delenv("RANK", raising=False)
+    monkeypatch.setattr(sys, "argv", ["bench.py", "--impl", "reference", "--workload", "al4_16", "--steps", "1",
+                                      "--warmup", "3", "--cpu-sample", "8"])
+    bench.main()
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert key in line, key
+    assert line["impl"] == "reference" and line["unit"] == bench.UNIT and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
+                           "d2h_bytes_per_step": 0}
