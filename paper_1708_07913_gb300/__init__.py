@@ -279,12 +279,14 @@ class SQCNN:
         rho_ref[, mu]), ...]; with mu the sample is seen as V - mu (the
         Fermi-level-referenced map).  Returns that mean loss."""
         total = 0.0
-        for i, item in enumerate(batch):
-            shape, V, ref = item[:3]
-            sq.sq_cnn_set_shift(self.net, item[3] if len(item) > 3 else 0.0)
-            rho = self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
-            total += sq.sq_cnn_backward(self.net, shape, V, ref, rho, accumulate=i > 0)
-        sq.sq_cnn_set_shift(self.net, 0.0)
+        try:
+            for i, item in enumerate(batch):
+                shape, V, ref = item[:3]
+                sq.sq_cnn_set_shift(self.net, item[3] if len(item) > 3 else 0.0)
+                rho = self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
+                total += sq.sq_cnn_backward(self.net, shape, V, ref, rho, accumulate=i > 0)
+        finally:
+            sq.sq_cnn_set_shift(self.net, 0.0)
         sq.sq_cnn_adam_step(self.net, lr, beta1, beta2, eps, grad_scale=1.0 / len(batch))
         return total / len(batch)
 
@@ -300,34 +302,32 @@ class SQCNN:
             sq.sq_cnn_set_shift(self.net, mu)
             return h3 * sq.sq_cnn_forward_sum(self.net, shape, V, rho)
 
-        lo, hi, width = -1.0, 1.0, 2.0
-        n_lo, n_hi = count(lo), count(hi)
-        for _ in range(20):
-            if n_lo <= n_electrons <= n_hi:
-                break
-            width *= 2.0
-            if n_lo > n_electrons:
-                lo -= width
-                n_lo = count(lo)
-            if n_hi < n_electrons:
-                hi += width
-                n_hi = count(hi)
-        else:
+        try:
+            lo, hi, width = -1.0, 1.0, 2.0
+            n_lo, n_hi = count(lo), count(hi)
+            for _ in range(20):
+                if n_lo <= n_electrons <= n_hi:
+                    break
+                width *= 2.0
+                if n_lo > n_electrons:
+                    lo -= width
+                    n_lo = count(lo)
+                if n_hi < n_electrons:
+                    hi += width
+                    n_hi = count(hi)
+            if not (n_lo <= n_electrons <= n_hi):
+                return None, None
+            for _ in range(steps):
+                mid = 0.5 * (lo + hi)
+                if count(mid) < n_electrons:
+                    lo = mid
+                else:
+                    hi = mid
+            mu = 0.5 * (lo + hi)
+            count(mu)                              # rho at the final shift
+            return rho, mu
+        finally:
             sq.sq_cnn_set_shift(self.net, 0.0)
-            return None, None
-        if not (n_lo <= n_electrons <= n_hi):
-            sq.sq_cnn_set_shift(self.net, 0.0)
-            return None, None
-        for _ in range(steps):
-            mid = 0.5 * (lo + hi)
-            if count(mid) < n_electrons:
-                lo = mid
-            else:
-                hi = mid
-        mu = 0.5 * (lo + hi)
-        count(mu)                                  # rho at the final shift
-        sq.sq_cnn_set_shift(self.net, 0.0)
-        return rho, mu
 
     def save(self, path):
         import numpy as np
