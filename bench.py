@@ -64,7 +64,7 @@ def parse():
     p.add_argument("--train-geometries", type=int, default=250, help="warmstart_c4: seeded training geometries")
     p.add_argument("--train-iters", type=int, default=8, help="warmstart_c4: SCF iterations kept per geometry")
     p.add_argument("--train-steps", type=int, default=1000, help="warmstart_c4: Adam steps")
-    p.add_argument("--max-scf", type=int, default=60, help="warmstart_c4, scf_*: SCF iteration limit")
+    p.add_argument("--max-scf", type=int, default=80, help="warmstart_c4, scf_*: SCF iteration limit")
     p.add_argument("--kerker", default="0.8,0.2", help="scf_*: k0,amin of the preconditioner, or 'none'")
     p.add_argument("--history", type=int, default=12, help="scf_*: mixing history")
     p.add_argument("--beta", type=float, default=0.3, help="scf_*: mixing parameter")
