@@ -65,8 +65,8 @@ def parse():
     p.add_argument("--train-iters", type=int, default=8, help="warmstart_c4: SCF iterations kept per geometry")
     p.add_argument("--train-steps", type=int, default=1000, help="warmstart_c4: Adam steps")
     p.add_argument("--max-scf", type=int, default=80, help="warmstart_c4, scf_*: SCF iteration limit")
-    p.add_argument("--kerker", default="0.8,0.2", help="scf_*: k0,amin of the preconditioner, or 'none'")
-    p.add_argument("--history", type=int, default=12, help="scf_*: mixing history")
+    p.add_argument("--kerker", default="0.5,0.1", help="scf_*: k0,amin of the preconditioner, or 'none'")
+    p.add_argument("--history", type=int, default=16, help="scf_*: mixing history")
     p.add_argument("--beta", type=float, default=0.3, help="scf_*: mixing parameter")
     p.add_argument("--period", type=int, default=1, help="scf_*: Pulay period (1: Anderson every step)")
     return p.parse_args()
@@ -755,7 +755,7 @@ def run_warmstart(a):
                                "n_pl=48, kT=0.05); training on one-cell 16^3 geometries",
                    "training_pairs": len(pairs), "training_geometries": a.train_geometries,
                    "scf_iterations_per_geometry": a.train_iters, "adam_steps": a.train_steps,
-                   "mixing": "Anderson, history 12, beta 0.3, Kerker (0.8, 0.2)", "best": best,
+                   "mixing": "Anderson, history 16, beta 0.3, Kerker (0.5, 0.1)", "best": best,
                    "parallelism": "single GPU"},
         "plain_iterations": res["plain"]["iterations"], "plain_converged": res["plain"]["converged"],
         "results": res,

@@ -74,8 +74,8 @@ def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=
     return losses, time.perf_counter() - t0
 
 
-def compare(nets, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=12,
-            kerker=(0.8, 0.2)):
+def compare(nets, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=16,
+            kerker=(0.5, 0.1)):
     """SCF iterations of ``wl`` from V_loc and from the warm start of each
     network in ``nets`` = {label: (net, fermi_referenced)}, all with the same
     mixer (Kerker-preconditioned unless ``kerker`` is None).  Returns
