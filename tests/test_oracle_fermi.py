@@ -6,7 +6,6 @@ Independent references: discrete orthogonality of Chebyshev polynomials,
 dense diagonalisation of the periodic finite-difference Hamiltonian (the
 periodic-region mode reduces SQ to e_q^T g(H) e_q), the free-electron
 Brillouin-zone integral, and exact invariants."""
-import math
 
 import numpy as np
 import pytest

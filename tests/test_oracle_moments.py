@@ -4,7 +4,6 @@ and Lanczos bounds (Section 3.2).
 Independent references: dense eigendecomposition of H_q, closed forms for
 rho^0..rho^2, the infinite-lattice (Brillouin-zone) value of the free-electron
 moments, and numpy's tridiagonal eigenvalues."""
-import math
 
 import numpy as np
 import pytest

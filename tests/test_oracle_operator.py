@@ -7,7 +7,6 @@ the nonlocal term, and translation covariance."""
 import math
 
 import numpy as np
-import pytest
 from scipy.special import erf
 
 import oracle
