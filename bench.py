@@ -734,11 +734,13 @@ def run_warmstart(a):
                                  sigma_disp=target.sigma_disp, nonlocal_=True, seed=0)
     clocks = ClockSampler(0)
     clocks.start()
-    pairs, t_data = wsm.training_pairs(tmpl, a.train_geometries, a.train_iters, seed=5000, device=str(dev))
+    pairs, t_data = wsm.training_pairs(tmpl, a.train_geometries, a.train_iters, seed=5000, device=str(dev),
+                                       mu_offsets=(-0.1, -0.05, 0.0, 0.05, 0.1))
     nets, t_train, losses = {}, {}, {}
     for label, fermi in (("warm_V", False), ("warm_V_minus_mu", True)):
-        net = SQCNN(True, 0, *wsm.input_scales(pairs, fermi_referenced=fermi), device=str(dev))
-        losses[label], t_train[label] = wsm.train(net, pairs, a.train_steps, fermi_referenced=fermi)
+        use = pairs if fermi else wsm.scf_pairs(pairs)
+        net = SQCNN(True, 0, *wsm.input_scales(use, fermi_referenced=fermi), device=str(dev))
+        losses[label], t_train[label] = wsm.train(net, use, a.train_steps, fermi_referenced=fermi)
         nets[label] = (net, fermi)
     res = wsm.compare(nets, target, tol=1e-6, max_iter=a.max_scf, device=str(dev))
     clk = clocks.stop()
@@ -754,6 +756,7 @@ def run_warmstart(a):
         "config": {"workload": "warmstart_c4: target al256_64 (4^3 cells, 256 atoms, 64^3 grid, 25^3 regions, "
                                "n_pl=48, kT=0.05); training on one-cell 16^3 geometries",
                    "training_pairs": len(pairs), "training_geometries": a.train_geometries,
+                   "fermi_level_offsets": [-0.1, -0.05, 0.0, 0.05, 0.1],
                    "scf_iterations_per_geometry": a.train_iters, "adam_steps": a.train_steps,
                    "mixing": "Anderson, history 16, beta 0.3, Kerker (0.5, 0.1)", "best": best,
                    "parallelism": "single GPU"},

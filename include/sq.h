@@ -46,7 +46,8 @@ extern "C" {
 
 typedef enum {
     SQ_OK = 0,
-    SQ_EINVAL = 1,      /* invalid argument (checked on the host)                    */
+    SQ_EINVAL = 1,      /* invalid argument (checked on the host; a non-finite       */
+                        /* potential value is detected on the device and latched)    */
     SQ_ECUDA = 2,       /* a CUDA runtime call or kernel launch failed               */
     SQ_EBOUNDS = 3,     /* spectrum outside [chi-zeta, chi+zeta]: |rho^j| > 1 + tol   */
     SQ_ENOCONV = 4,     /* Fermi-level bracket does not contain N_e                  */
@@ -108,7 +109,9 @@ int sq_set_stream(sq_ctx *ctx, void *cuda_stream);
  * region; exactly n_lanczos steps (fewer only on breakdown, beta <= 1e-10 *
  * scale); extreme Ritz values by Sturm bisection in FP64; both ends widened
  * by margin * max(theta_max - theta_min, 1 Ha).
- *   V     device, N_d FP64 effective potential
+ *   V     device, N_d FP64 effective potential; a NaN or infinite value
+ *         (here or in sq_moments) latches SQ_EINVAL, returned by the next
+ *         synchronising call
  *   chi   device, N_d FP64 output
  *   zeta  device, N_d FP64 output
  *   1 <= n_lanczos <= 512, 0 <= margin < 1. */

@@ -282,6 +282,9 @@ class SQCNN:
         try:
             for i, item in enumerate(batch):
                 shape, V, ref = item[:3]
+                if len(item) > 3:
+                    lo, hi = getattr(self, "mu_seen", (item[3], item[3]))
+                    self.mu_seen = (min(lo, item[3]), max(hi, item[3]))
                 sq.sq_cnn_set_shift(self.net, item[3] if len(item) > 3 else 0.0)
                 rho = self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
                 total += sq.sq_cnn_backward(self.net, shape, V, ref, rho, accumulate=i > 0)
@@ -290,37 +293,52 @@ class SQCNN:
         sq.sq_cnn_adam_step(self.net, lr, beta1, beta2, eps, grad_scale=1.0 / len(batch))
         return total / len(batch)
 
-    def predict_electrons(self, shape, V, n_electrons, h, out=None, steps=50):
-        """Density of V for a network trained on V - mu: the shift mu is
-        found by bisection so that h^3 sum rho = n_electrons (the density
-        rises with mu).  Returns (rho, mu), or (None, None) when no bracket
-        is found within 20 doublings of the interval."""
+    def predict_electrons(self, shape, V, n_electrons, h, out=None, steps=50, center=None, half_width=None,
+                          points=33):
+        """Density of V for a network trained on V - mu: the shift mu with
+        h^3 sum rho = n_electrons.  N(mu) is evaluated on ``points`` shifts
+        evenly spread over center +- half_width (default: the middle of the
+        Fermi levels seen in training, and the larger of 2 v_scale and the
+        training range), the sign change of N - n_electrons nearest the
+        centre is kept, and bisection narrows it in ``steps`` halvings (a
+        trained network need not be monotone in mu far from its training
+        range, so no direction is assumed).  Returns (rho, mu), or
+        (None, None) when N never crosses n_electrons on the scan; the scan
+        is kept in ``self.last_scan`` = (shifts, counts) for diagnosis."""
         rho = out if out is not None else self.torch.empty(V.numel(), dtype=self.torch.float64, device=self.device)
         h3 = float(h) ** 3
+        lo_seen, hi_seen = getattr(self, "mu_seen", (0.0, 0.0))
+        c = 0.5 * (lo_seen + hi_seen) if center is None else float(center)
+        w = max(2.0 * self.scales[1], hi_seen - lo_seen) if half_width is None else float(half_width)
 
         def count(mu):
             sq.sq_cnn_set_shift(self.net, mu)
             return h3 * sq.sq_cnn_forward_sum(self.net, shape, V, rho)
 
         try:
-            lo, hi, width = -1.0, 1.0, 2.0
-            n_lo, n_hi = count(lo), count(hi)
-            for _ in range(20):
-                if n_lo <= n_electrons <= n_hi:
-                    break
-                width *= 2.0
-                if n_lo > n_electrons:
-                    lo -= width
-                    n_lo = count(lo)
-                if n_hi < n_electrons:
-                    hi += width
-                    n_hi = count(hi)
-            if not (n_lo <= n_electrons <= n_hi):
+            shifts = [c - w + 2.0 * w * k / (points - 1) for k in range(points)]
+            counts = [count(m) for m in shifts]
+            self.last_scan = (shifts, counts)
+            f = [n - n_electrons for n in counts]
+            best = None
+            for k in range(points - 1):
+                if f[k] == 0.0 or (f[k] < 0.0) != (f[k + 1] < 0.0):
+                    d = abs(0.5 * (shifts[k] + shifts[k + 1]) - c)
+                    if best is None or d < best[0]:
+                        best = (d, k)
+            if best is None:
                 return None, None
+            k = best[1]
+            lo, hi, f_lo = shifts[k], shifts[k + 1], f[k]
+            if f_lo == 0.0:
+                hi = lo
             for _ in range(steps):
+                if hi == lo:
+                    break
                 mid = 0.5 * (lo + hi)
-                if count(mid) < n_electrons:
-                    lo = mid
+                fm = count(mid) - n_electrons
+                if (fm < 0.0) == (f_lo < 0.0):
+                    lo, f_lo = mid, fm
                 else:
                     hi = mid
             mu = 0.5 * (lo + hi)
@@ -331,7 +349,8 @@ class SQCNN:
 
     def save(self, path):
         import numpy as np
-        np.savez(path, params=self.params(), scales=np.array(self.scales), bf16=np.array(self.bf16))
+        np.savez(path, params=self.params(), scales=np.array(self.scales), bf16=np.array(self.bf16),
+                 mu_seen=np.array(getattr(self, "mu_seen", (0.0, 0.0))))
 
     @classmethod
     def load(cls, path, device="cuda:0"):
@@ -339,6 +358,8 @@ class SQCNN:
         d = np.load(path)
         net = cls(bool(d["bf16"]), 0, *d["scales"], device=device)
         net.set_params(d["params"], *d["scales"])
+        if "mu_seen" in d:
+            net.mu_seen = tuple(float(x) for x in d["mu_seen"])
         return net
 
     def close(self):

@@ -92,6 +92,7 @@ int take_device_error(sq_ctx* c)
     unsigned z = 0;
     if (cudaMemcpyAsync(c->d_err, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return SQ_ECUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+    if (e & ERR_NONFINITE) return SQ_EINVAL;
     if (e & ERR_CAPACITY) return SQ_ECAPACITY;
     return SQ_EBOUNDS;
 }

@@ -32,6 +32,7 @@ constexpr int STAGE = 16;            // row entries staged per warp at a time in
 // Error bits latched on the device (combined into one sq_status on the host).
 constexpr unsigned ERR_BOUNDS = 1u;
 constexpr unsigned ERR_CAPACITY = 2u;
+constexpr unsigned ERR_NONFINITE = 4u;   // a potential value that is NaN or infinite
 
 struct AtomTab {                     // per-atom projector geometry (device)
     int lo[3];

@@ -18,7 +18,8 @@ namespace sq {
 // Potential with halo: Vp[k'][j'][i'] = V[(k'-m) mod n3][(j'-m) mod n2][(i'-m) mod n1]
 // ------------------------------------------------------------------------
 template <typename T>
-__global__ void vpad_kernel(const double* __restrict__ V, T* __restrict__ Vp, int n1, int n2, int n3, int m)
+__global__ void vpad_kernel(const double* __restrict__ V, T* __restrict__ Vp, int n1, int n2, int n3, int m,
+                            unsigned* err)
 {
     const int P1 = n1 + 2 * m, P2 = n2 + 2 * m, P3 = n3 + 2 * m;
     const long long tot = (long long)P1 * P2 * P3;
@@ -30,7 +31,9 @@ __global__ void vpad_kernel(const double* __restrict__ V, T* __restrict__ Vp, in
         int a = ((i - m) % n1 + n1) % n1;
         int b = ((j - m) % n2 + n2) % n2;
         int c = ((k - m) % n3 + n3) % n3;
-        Vp[t] = (T)V[a + (long long)n1 * (b + (long long)n2 * c)];
+        const double v = V[a + (long long)n1 * (b + (long long)n2 * c)];
+        if (!isfinite(v)) atomicOr(err, ERR_NONFINITE);
+        Vp[t] = (T)v;
     }
 }
 
@@ -40,9 +43,9 @@ int launch_build_vpad(sq_ctx* ctx, const double* V)
     long long tot = (long long)g.P1 * g.P2 * (g.n3 + 2 * g.m);
     int blocks = (int)std::min<long long>((tot + 255) / 256, (long long)ctx->sm_count * 16);
     if (ctx->precision == SQ_FP32)
-        vpad_kernel<float><<<blocks, 256, 0, ctx->stream>>>(V, (float*)ctx->Vp, g.n1, g.n2, g.n3, g.m);
+        vpad_kernel<float><<<blocks, 256, 0, ctx->stream>>>(V, (float*)ctx->Vp, g.n1, g.n2, g.n3, g.m, ctx->d_err);
     else
-        vpad_kernel<double><<<blocks, 256, 0, ctx->stream>>>(V, (double*)ctx->Vp, g.n1, g.n2, g.n3, g.m);
+        vpad_kernel<double><<<blocks, 256, 0, ctx->stream>>>(V, (double*)ctx->Vp, g.n1, g.n2, g.n3, g.m, ctx->d_err);
     ctx->launches++;
     return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;
 }

@@ -23,11 +23,32 @@ import synth
 from . import SQ_FP32, SQCNN, SQSCF, SQSolver, warm_start_potential
 
 
-def training_pairs(template, n_geometries, iters, seed, precision=SQ_FP32, device="cuda:0"):
-    """(shape, V_in, rho, mu) device pairs (mu: the SQ Fermi level of that
-    solve) from ``iters`` SCF iterations on each of ``n_geometries``
-    geometries of ``template`` (a synth.Workload), seeds seed, seed + 1, ...
-    Returns (pairs, seconds)."""
+def pair_collector(solver, kT, pairs, mu_offsets=(0.0,)):
+    """An ``on_step`` callback for SQSCF.run that appends (shape, V_in, rho,
+    mu', offset) to ``pairs`` for every mu' = mu + offset.  The densities at shifted
+    Fermi levels come from the same SQ solve: the moments do not depend on
+    mu (Section 3.2), so each is one sq_density_energy call at mu'.  They
+    teach a network fed V - mu how the density moves with the Fermi level.
+    The solver's own density (the SCF's) is restored before returning."""
+    shape = solver.shape
+
+    def on_step(V, rho, mu):
+        keep = rho.clone()
+        for d in mu_offsets:
+            if d == 0.0:
+                pairs.append((shape, V.clone(), keep.clone(), float(mu), 0.0))
+            else:
+                solver.density_energy(float(mu) + d, kT)
+                pairs.append((shape, V.clone(), solver.rho.clone(), float(mu) + d, float(d)))
+        rho.copy_(keep)
+    return on_step
+
+
+def training_pairs(template, n_geometries, iters, seed, precision=SQ_FP32, device="cuda:0", mu_offsets=(0.0,)):
+    """(shape, V_in, rho, mu, offset) device pairs (mu: the SQ Fermi level
+    of that solve plus one of ``mu_offsets``; see pair_collector) from ``iters`` SCF
+    iterations on each of ``n_geometries`` geometries of ``template`` (a
+    synth.Workload), seeds seed, seed + 1, ...  Returns (pairs, seconds)."""
     import torch
     pairs = []
     t0 = time.perf_counter()
@@ -37,13 +58,17 @@ def training_pairs(template, n_geometries, iters, seed, precision=SQ_FP32, devic
         solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=device)
         V_loc = torch.from_numpy(s.V.ravel().copy()).to(device)
         scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, margin=wl.margin)
-        shape = (wl.n,) * 3
-        scf.run(tol=0.0, max_iter=iters,
-                on_step=lambda V, rho, mu: pairs.append((shape, V.clone(), rho.clone(), float(mu))))
+        scf.run(tol=0.0, max_iter=iters, on_step=pair_collector(solver, wl.kT, pairs, mu_offsets))
         scf.close()
         solver.close()
     torch.cuda.synchronize()
     return pairs, time.perf_counter() - t0
+
+
+def scf_pairs(pairs):
+    """The pairs at the SCF's own Fermi level (offset 0): the only ones a
+    network fed V itself (not V - mu) can learn from."""
+    return [p for p in pairs if len(p) < 5 or p[4] == 0.0]
 
 
 def input_scales(pairs, fermi_referenced=True):

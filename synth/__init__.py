@@ -91,6 +91,10 @@ WORKLOADS = {
     # 2x2x2-cell (32^3) grid, so the same kernels run on 30% of the nodes
     "al32_32": Workload("al32_32", cells=2, n=32, r_cut=6.0, npl=48, kT=0.05,
                         sigma_disp=0.15, nonlocal_=True, seed=1713),
+    # profiling case of the scale workload: its region (29^3), degree,
+    # temperature, displacements and projectors on a 2x2x2-cell (32^3) grid
+    "al32_32_r7": Workload("al32_32_r7", cells=2, n=32, r_cut=7.0, npl=64, kT=0.1,
+                           sigma_disp=0.2, nonlocal_=True, seed=1714),
 }
 
 

@@ -1,4 +1,5 @@
-"""Write full-grid oracle results for a workload to tests/golden/<name>_oracle.json.
+"""Write full-grid oracle results for a workload to tests/golden/<name>_oracle.json
+and its full-grid density (float64, node order) to tests/golden/<name>_oracle_rho.npy.
 
 Calls only oracle/ and synth/: every node's Lanczos bounds and Chebyshev
 moments are computed by the CPU oracle (spread over spawned worker
@@ -78,6 +79,7 @@ def main():
     path = os.path.join(ROOT, "tests", "golden", f"{a.name}_oracle.json")
     with open(path, "w") as f:
         json.dump(out, f)
+    np.save(os.path.join(ROOT, "tests", "golden", f"{a.name}_oracle_rho.npy"), rho)
     print(f"wrote {path} in {time.time() - t0:.0f} s: mu={mu} e_band={eb} e_ent={es} N={ne}")
 
 

@@ -98,8 +98,7 @@ def test_al4_fp32_own_bounds(al4):
     assert abs(g["n_elec"] - s.wl.n_electrons) < 1e-9 * s.wl.n_electrons
 
 
-@pytest.mark.parametrize("name,precision,count", [
-    ("al108_48", SQ_FP64, 12), ("al108_48", SQ_FP32, 24), ("al2048_128", SQ_FP32, 8)])
+@pytest.mark.parametrize("name,precision,count", [("al108_48", SQ_FP64, 12), ("al108_48", SQ_FP32, 24)])
 def test_full_size_sampled_nodes(name, precision, count):
     """Full-size workload in the benchmark's launch configuration; the oracle
     recomputes bounds and moments of a seeded node sample one by one."""
@@ -138,6 +137,63 @@ def test_full_size_sampled_nodes(name, precision, count):
     # is not an oracle-only expectation, so the density itself is checked on
     # the small workloads; here only its integral and sign
     assert torch.all(solver.rho >= -1e-8).item()
+    solver.close()
+
+
+def test_scale_workload_fp32_sampled_density_and_energy():
+    """The scale workload (8^3 FCC cells, 2048 atoms, 128^3 grid, 29^3
+    regions, n_pl = 64, s + 3p, FP32 recurrence with FP64 moments), whole
+    grid in the benchmark's launch configuration.  The oracle recomputes the
+    bounds and moments of 64 seeded nodes one by one; with its bounds
+    injected on those nodes, the GPU moments, and the density and band /
+    entropy energy of those nodes at a fixed test-chosen Fermi level
+    (Eqs. ElectronDensity, Eband, Entropy), must match the oracle's.  The
+    whole-grid electron count at the GPU's own Fermi level must equal N_e,
+    and every moment must stay inside [-1, 1] (the enclosure guard)."""
+    s = synth.make_system("al2048_128")
+    wl = s.wl
+    assert (wl.m, wl.npl) == (14, 64)
+    nodes = synth.sample_nodes(wl.n_nodes, 64, seed=29)
+    mu_fixed = -0.1                                   # Ha; near this system's Fermi level
+    osys = oracle.OracleSystem.from_synth(s)
+    ochi, ozeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
+    omom = osys.moments(nodes, ochi, ozeta, wl.npl)
+    oW = oracle.cc_weights(omom)
+    orho, oeb, oes, one = oracle.density_energy(oW, ochi, ozeta, mu_fixed, wl.kT, wl.h)
+    assert 0.2 * orho.max() < orho.mean()             # the fixed level fills these nodes
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP32, device=DEV)
+    V = _dev(s.V)
+    chi, zeta = solver.bounds(V, wl.n_lanczos, wl.margin)
+    np.testing.assert_allclose(chi.cpu().numpy()[nodes], ochi, rtol=2e-4)
+    np.testing.assert_allclose(zeta.cpu().numpy()[nodes], ozeta, rtol=2e-4)
+    idx = torch.from_numpy(nodes).to(DEV)
+    chi[idx] = _dev(ochi)
+    zeta[idx] = _dev(ozeta)
+    mom = solver.compute_moments(V, chi, zeta)
+    gm = mom[idx].cpu().numpy()
+    np.testing.assert_allclose(gm, omom, rtol=0, atol=FP32_MOM)
+    assert torch.all(mom.abs() <= 1 + 1e-4).item()
+    # the whole grid at the GPU's own Fermi level: electron count conserved
+    mu = solver.fermi_level(wl.n_electrons, wl.kT, chi, zeta)
+    eb, es, ne = solver.density_energy(mu, wl.kT, chi, zeta)
+    assert abs(ne - wl.n_electrons) < 1e-8 * wl.n_electrons and es <= 0.0
+    # density of the sampled nodes at the fixed level
+    solver.density_energy(mu_fixed, wl.kT, chi, zeta)
+    grho = solver.rho[idx].cpu().numpy()
+    assert np.abs(grho - orho).max() < FP32_RHO * orho.max()
+    assert _rel2(grho, orho) < FP32_RHO
+    # band and entropy energy of the sampled nodes: the density step on those
+    # nodes alone (the allocation-free entry point runs the same quadrature on
+    # any node list; it matches sq_density_energy in tests/test_zz_no_alloc.py)
+    rho_s = torch.empty(len(nodes), dtype=torch.float64, device=DEV)
+    geb, ges, gne = sq.sq_density_energy_noalloc((len(nodes), 1, 1), wl.h, wl.npl, mom[idx].contiguous(),
+                                                 chi[idx].contiguous(), zeta[idx].contiguous(), mu_fixed, wl.kT,
+                                                 rho_s)
+    # the FP32 target is 1e-5 Ha per atom; the sample stands for
+    # n_atoms * 64 / N_d atoms of the crystal
+    atoms = wl.n_atoms * len(nodes) / wl.n_nodes
+    assert abs(geb - oeb) < FP32_E_PER_ATOM * atoms and abs(ges - oes) < FP32_E_PER_ATOM * atoms
+    assert abs(gne - one) < FP32_RHO * one
     solver.close()
 
 
@@ -240,6 +296,18 @@ def test_errors_are_reported_not_faulted():
     with pytest.raises(SQError) as e:
         solver.fermi_level(2.0 * wl.n_nodes + 1, wl.kT)
     assert e.value.code == sq.SQ_EINVAL
+    # a NaN and an infinity in the potential: found by the halo copy on the
+    # device, latched, and returned as SQ_EINVAL by the next synchronising call
+    for bad in (float("nan"), float("inf")):
+        Vbad = V.clone()
+        Vbad[wl.n_nodes // 3] = bad
+        solver.bounds(Vbad, wl.n_lanczos, wl.margin)
+        with pytest.raises(SQError) as e:
+            sq.sq_sync(solver.ctx)
+        assert e.value.code == sq.SQ_EINVAL
+        # the error is cleared once reported; the context stays usable
+        out = solver.solve(V, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)
+        assert abs(out["n_elec"] - wl.n_electrons) < 1e-8
     solver.close()
 
 

@@ -69,7 +69,11 @@ def test_train_then_warm_start(tmp_path):
 def test_fermi_referenced_warm_start():
     """The network trained on V - mu; each surrogate step finds mu so that
     the predicted density holds N_e electrons; the SCF from that start
-    reaches the same fixed point."""
+    reaches the same fixed point.  Every SQ solve also gives the densities
+    at Fermi levels 0.05 and 0.1 Ha either side of its own (same moments),
+    so the network sees how the density moves with mu and its electron
+    count N(mu) rises through N_e near the training Fermi levels."""
+    from paper_1708_07913_gb300 import warmstart as wsm
     wl = synth.custom_workload("ws8m", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
                                seed=1751)
     s = synth.make_system(wl)
@@ -79,20 +83,26 @@ def test_fermi_referenced_warm_start():
     pairs = []
     scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT)
     plain = scf.run(tol=1e-6, max_iter=60,
-                    on_step=lambda V, rho, mu: pairs.append((shape, V.clone(), rho.clone(), float(mu))))
+                    on_step=wsm.pair_collector(solver, wl.kT, pairs, (-0.1, -0.05, 0.0, 0.05, 0.1)))
+    assert plain["converged"] and len(pairs) == 5 * plain["iterations"]
     rho_plain = plain["rho"].cpu().numpy().copy()
-    mus = np.array([p[3] for p in pairs])
+    scf_only = wsm.scf_pairs(pairs)
+    assert len(scf_only) == plain["iterations"]
+    # the collector restores the SCF's own density: the last SCF pair is the converged density
+    np.testing.assert_array_equal(scf_only[-1][2].cpu().numpy(), rho_plain)
+    mus = np.array([p[3] for p in scf_only])
     Vm = np.concatenate([p[1].cpu().numpy() - p[3] for p in pairs])
     net = SQCNN(bf16=True, seed=4, v_shift=float(Vm.mean()), v_scale=float(Vm.std()),
-                rho_scale=float(pairs[-1][2].mean().item()))
+                rho_scale=float(np.mean([p[2].mean().item() for p in pairs])))
     first = net.train_step(pairs[:3], lr=3e-3)
     rng = np.random.default_rng(1)
     for _ in range(60):
-        idx = rng.choice(len(pairs), size=min(3, len(pairs)), replace=False)
+        idx = rng.choice(len(pairs), size=3, replace=False)
         last = net.train_step([pairs[i] for i in idx], lr=3e-3)
     assert np.isfinite(last) and last < 0.5 * first
-    rho, mu = net.predict_electrons(shape, pairs[-1][1], wl.n_electrons, wl.h)
-    assert rho is not None and mus.min() - 1.0 < mu < mus.max() + 1.0
+    rho, mu = net.predict_electrons(shape, scf_only[-1][1], wl.n_electrons, wl.h)
+    assert rho is not None, f"no crossing of N_e on the scan: {net.last_scan}"
+    assert mus.min() - 1.0 < mu < mus.max() + 1.0
     # bfloat16 storage rounds the shifted input, so N(mu) is a fine staircase: the
     # bisection lands on a step, within one step of N_e
     assert abs(wl.h ** 3 * rho.sum().item() - wl.n_electrons) < 1e-3 * wl.n_electrons

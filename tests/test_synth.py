@@ -9,7 +9,8 @@ import synth
 
 
 @pytest.mark.parametrize("name,cells,n,atoms,m", [("al4_16", 1, 16, 4, 6), ("al108_48", 3, 48, 108, 12),
-                                                  ("al32_32", 2, 32, 32, 12), ("al256_64", 4, 64, 256, 12)])
+                                                  ("al32_32", 2, 32, 32, 12), ("al256_64", 4, 64, 256, 12),
+                                                  ("al32_32_r7", 2, 32, 32, 14), ("al2048_128", 8, 128, 2048, 14)])
 def test_named_workloads(name, cells, n, atoms, m):
     wl = synth.WORKLOADS[name]
     assert (wl.cells, wl.n, wl.n_atoms, wl.m) == (cells, n, atoms, m)

@@ -2,7 +2,9 @@
 the library allocate device memory (programs that reserve all GPU memory for
 their own allocator, or settle their memory budget at start-up) -- must give
 the same density, band energy, entropy and electron count as
-sq_density_energy, call after call.  This file is named to be collected last.
+sq_density_energy, call after call, and as the CPU oracle's density step
+(Eqs. ElectronDensity, Eband and Entropy) on the oracle's own moments,
+bounds and Fermi level.  This file is named to be collected last.
 """
 import numpy as np
 import pytest
@@ -14,7 +16,29 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+import oracle  # noqa: E402
 from paper_1708_07913_gb300 import SQ_FP64, SQSolver, build, sq  # noqa: E402
+
+
+def test_noalloc_matches_oracle_twice():
+    """al4_16, every node: the inputs (bounds, moments, Fermi level) are the
+    oracle's, so both sides evaluate the same quadrature; FP64 to 1e-10."""
+    build()
+    s = synth.make_system("al4_16")
+    wl = s.wl
+    ref = oracle.solve(oracle.OracleSystem.from_synth(s), wl.npl, wl.kT, wl.n_electrons, wl.n_lanczos, wl.margin)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).cuda()   # noqa: E731
+    mom, chi, zeta = dev(ref["moments"]), dev(ref["chi"]), dev(ref["zeta"])
+    for _ in range(2):
+        rho = torch.full((wl.n_nodes,), float("nan"), dtype=torch.float64, device="cuda")
+        eb, es, ne = sq.sq_density_energy_noalloc((wl.n, wl.n, wl.n), wl.h, wl.npl, mom, chi, zeta, ref["mu"],
+                                                  wl.kT, rho)
+        got = rho.cpu().numpy()
+        assert np.linalg.norm(got - ref["rho"]) < 1e-10 * np.linalg.norm(ref["rho"])
+        assert np.abs(got - ref["rho"]).max() < 1e-10 * ref["rho"].max()
+        assert abs(eb - ref["e_band"]) < 1e-10 * abs(ref["e_band"])
+        assert abs(es - ref["e_ent"]) < 1e-10 * abs(ref["e_ent"])
+        assert abs(ne - ref["n_elec"]) < 1e-10 * abs(ref["n_elec"])
 
 
 @pytest.mark.parametrize("name", ["al4_16", "al108_48"])
