@@ -17,6 +17,11 @@ int region_config_f32(int m, int which, size_t extra, int* bps, size_t* smem);
 int region_config_f64(int m, int which, size_t extra, int* bps, size_t* smem);
 int region_launch_f32(int m, int which, const RegionArgs<float>& a, size_t extra, int blocks, cudaStream_t st);
 int region_launch_f64(int m, int which, const RegionArgs<double>& a, size_t extra, int blocks, cudaStream_t st);
+int cluster_nc(int m);
+int cluster_config_f32_lo(int m, int which, int ccap, int npl, int* clusters, size_t* smem);
+int cluster_config_f32_hi(int m, int which, int ccap, int npl, int* clusters, size_t* smem);
+int cluster_launch_f32_lo(int m, int which, const RegionArgs<float>& a, int clusters, size_t smem, cudaStream_t st);
+int cluster_launch_f32_hi(int m, int which, const RegionArgs<float>& a, int clusters, size_t smem, cudaStream_t st);
 }  // namespace sq
 
 using namespace sq;
@@ -258,6 +263,37 @@ RegionArgs<T> region_args(sq_ctx* c)
     return a;
 }
 
+// FP32 cluster kernels (sq_cluster.cuh) for this context when
+// SQ_REGION_KERNEL=cluster is set in the environment, its region size has
+// one and its projector candidates fit; otherwise the single-CTA kernels,
+// which measure faster on the benchmark workloads.  Sets c->cl_nc (0: none).
+int select_cluster_kernels(sq_ctx* c)
+{
+    c->cl_nc = 0;
+    if (c->precision != SQ_FP32 || cluster_nc(c->g.m) == 0) return SQ_OK;
+    const char* env = getenv("SQ_REGION_KERNEL");
+    if (!env || strcmp(env, "cluster") != 0) return SQ_OK;
+    const int ccap = c->ccap;                               // the kernels size their tables by it too
+    for (int which = 0; which < 2; ++which) {
+        const int rc = c->g.m <= 9 ? cluster_config_f32_lo(c->g.m, which, ccap, c->npl, &c->cl_clusters[which],
+                                                           &c->cl_smem[which])
+                                   : cluster_config_f32_hi(c->g.m, which, ccap, c->npl, &c->cl_clusters[which],
+                                                           &c->cl_smem[which]);
+        if (rc == SQ_EUNSUPPORTED) return SQ_OK;           // candidates do not fit: single-CTA kernels
+        if (rc) return rc;
+    }
+    c->cl_nc = cluster_nc(c->g.m);
+    return SQ_OK;
+}
+
+// Launch a cluster kernel on `blocks` CTAs (rounded down to whole clusters).
+int cluster_launch(sq_ctx* c, int which, const RegionArgs<float>& a, int blocks)
+{
+    const int clusters = std::max(1, blocks / c->cl_nc);
+    return c->g.m <= 9 ? cluster_launch_f32_lo(c->g.m, which, a, clusters, c->cl_smem[which], c->stream)
+                       : cluster_launch_f32_hi(c->g.m, which, a, clusters, c->cl_smem[which], c->stream);
+}
+
 // Dynamic shared memory beyond the region vectors: the moments kernel (which
 // = 0) keeps its per-node moment sums there; both keep the projector tables
 // there when they fit.
@@ -268,6 +304,12 @@ size_t region_extra(const sq_ctx* c, int which)
 
 int region_blocks(sq_ctx* c, int which, int* blocks)
 {
+    if (c->cl_nc > 0) {                  // cluster kernels: CTAs of every resident cluster
+        long long b = (long long)c->cl_clusters[which] * c->cl_nc;
+        if (b > c->g.Nd * c->cl_nc) b = c->g.Nd * c->cl_nc;
+        *blocks = (int)b;
+        return SQ_OK;
+    }
     int bps = 0;
     size_t smem = 0;
     int rc = c->precision == SQ_FP32 ? region_config_f32(c->g.m, which, region_extra(c, which), &bps, &smem)
@@ -306,7 +348,8 @@ int enqueue_bounds(sq_ctx* c, int blocks, int n_lanczos, double margin, double* 
     if (c->precision == SQ_FP32) {
         RegionArgs<float> a = region_args<float>(c);
         a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
-        rc = region_launch_f32(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
+        rc = c->cl_nc > 0 ? cluster_launch(c, 1, a, blocks)
+                          : region_launch_f32(c->g.m, 1, a, region_extra(c, 1), blocks, c->stream);
     } else {
         RegionArgs<double> a = region_args<double>(c);
         a.n_lanczos = n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
@@ -324,7 +367,8 @@ int enqueue_moments(sq_ctx* c, int blocks, const double* chi, const double* zeta
     if (c->precision == SQ_FP32) {
         RegionArgs<float> a = region_args<float>(c);
         a.chi = chi; a.zeta = zeta; a.moments = moments;
-        rc = region_launch_f32(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
+        rc = c->cl_nc > 0 ? cluster_launch(c, 0, a, blocks)
+                          : region_launch_f32(c->g.m, 0, a, region_extra(c, 0), blocks, c->stream);
     } else {
         RegionArgs<double> a = region_args<double>(c);
         a.chi = chi; a.zeta = zeta; a.moments = moments;
@@ -589,6 +633,7 @@ int sq_setup_grid(sq_ctx** out, int n1, int n2, int n3, double h, int fd_half_or
     } else {
         c->ntile[0] = c->ntile[1] = c->ntile[2] = 1;
     }
+    if ((rcode = select_cluster_kernels(c))) { free_ctx(c); return rcode; }
     // projector tables of the candidates in shared memory when they fit next
     // to the region vectors (both kernels must accept the size)
     int bm = 0, bl = 0;
@@ -600,7 +645,8 @@ int sq_setup_grid(sq_ctx** out, int n1, int n2, int n3, double h, int fd_half_or
     if ((rcode = region_blocks(c, 0, &bm)) || (rcode = region_blocks(c, 1, &bl))) { free_ctx(c); return rcode; }
     c->grid_blocks = std::max(bm, bl);
     c->scratch_bytes_per_cta = scratch_layout(m, tsz).total;
-    if ((rcode = dev_alloc(&c->d_scratch, c->scratch_bytes_per_cta * c->grid_blocks))) { free_ctx(c); return rcode; }
+    if (c->cl_nc == 0 &&               // the cluster kernels keep everything in shared memory
+        (rcode = dev_alloc(&c->d_scratch, c->scratch_bytes_per_cta * c->grid_blocks))) { free_ctx(c); return rcode; }
     c->red_blocks = c->sm_count * 4;
     if ((rcode = dev_alloc(&c->d_W, sizeof(double) * c->g.Nd * (npl + 1))) ||
         (rcode = dev_alloc(&c->d_red, sizeof(double) * 3 * c->red_blocks)) ||

@@ -129,6 +129,12 @@ struct sq_ctx {
     int* d_tile_start;
     int4* d_tile_cand;
     int ntile[3];
+    // FP32 cluster region kernels (sq_cluster.cuh): cluster size (0: the
+    // single-CTA kernels), resident clusters and dynamic shared memory, per
+    // kernel (0 moments, 1 Lanczos)
+    int cl_nc;
+    int cl_clusters[2];
+    size_t cl_smem[2];
     // per-CTA scratch
     int grid_blocks;                 // resident CTAs used for the region kernels
     size_t scratch_bytes_per_cta;

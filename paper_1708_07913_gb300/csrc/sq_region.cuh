@@ -24,11 +24,19 @@ namespace sq {
 template <int M>
 struct Geo {
     static constexpr int S = 2 * M + 1;
-    static constexpr int PX = S + 6;
-    static constexpr int PY = S + 6;
+    // Compact form for 27^3 and 29^3 regions (m = 13, 14): rows of pitch S+4
+    // (4 zero columns) and planes of exactly S rows, so that two vectors fit a
+    // CTA's shared memory (two fully padded 29^3 vectors would not); the
+    // stencil then masks the x neighbours at distance 5 and 6 of the edge
+    // columns and the y neighbours that fall outside the region, instead of
+    // reading zero halos.  LEAD and the 6-element tail keep every x-neighbour
+    // address inside the buffer.
+    static constexpr bool CY = (M == 13 || M == 14);
+    static constexpr int PX = CY ? S + 4 : S + 6;
+    static constexpr int PY = CY ? S : S + 6;
     static constexpr int PLANE = PX * PY;
-    static constexpr int LEAD = 6 * PX + 6;
-    static constexpr int ELEMS = LEAD + S * PLANE;
+    static constexpr int LEAD = CY ? 6 : 6 * PX + 6;
+    static constexpr int ELEMS = LEAD + S * PLANE + (CY ? 6 : 0);
     static constexpr int NS = S * S * S;
     static constexpr int NT = 32 * S;     // one warp per region row y, lane = x (lanes >= S idle)
     static constexpr int NW = S;
@@ -806,11 +814,11 @@ __device__ void nl_update_red(const RegionArgs<T>& a, const CtaScratch<T>& sc, T
 //        to sec, which becomes t^{i-1}.
 //   The thread accumulates out.out and out.t^i over its column.
 // RECUR = false (Lanczos): out = w goes to sec; t is left in place; the
-//   thread accumulates out.t.
+//   thread accumulates out.out, out.t and t.t.
 // ------------------------------------------------------------------------
-template <typename T, int M, bool RECUR, bool DB>
+template <typename T, int M, bool RECUR, bool DB, bool YEDGE = false>
 __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* vwin, T s, T dshift,
-                              T& acc_a, T& acc_b, double* centre_out)
+                              T& acc_a, T& acc_b, T& acc_c, double* centre_out)
 {
     using G = Geo<M>;
     using SV = Sec<M, DB>;
@@ -830,7 +838,7 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
     T vq[VD];
 #pragma unroll
     for (int d = 0; d < VD; ++d) vq[d] = (active && d < G::S) ? vcol[d * vplane] : T(0);
-    T aa = 0, ab = 0;
+    T aa = 0, ab = 0, ac = 0;
 #pragma unroll
     for (int z = 0; z < G::S; ++z) {
         T out = 0;
@@ -842,7 +850,22 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
             T lap = 0;
 #pragma unroll
             for (int d = 1; d <= FD_NO; ++d) {
-                T nb = (p[d] + p[-d]) + (p[d * G::PX] + p[-d * G::PX]) + (q[6 + d] + q[6 - d]);
+                T xp = p[d], xm = p[-d];
+                if constexpr (G::CY) {                 // beyond the 4 zero columns: the next/previous row
+                    if (d >= 5) {
+                        if (x + d >= G::S) xp = T(0);
+                        if (x < d) xm = T(0);
+                    }
+                }
+                T yp, ym;
+                if constexpr (G::CY && YEDGE) {        // no zero rows: outside the region is zero
+                    yp = (y + d < G::S) ? p[d * G::PX] : T(0);
+                    ym = (y >= d) ? p[-d * G::PX] : T(0);
+                } else {
+                    yp = p[d * G::PX];
+                    ym = p[-d * G::PX];
+                }
+                T nb = (xp + xm) + (yp + ym) + (q[6 + d] + q[6 - d]);
                 lap += a.wd[d] * nb;
             }
             T hv = (vz + dshift) * c + lap;
@@ -858,7 +881,9 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
                 if (x == M && y == M && z == M) *centre_out = (double)out;
             } else {
                 bcol[z * SV::ZS] = out;
+                aa += out * out;
                 ab += out * c;
+                ac += c * c;
             }
         }
 #pragma unroll
@@ -867,6 +892,7 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
     }
     acc_a = aa;
     acc_b = ab;
+    acc_c = ac;
 }
 
 // ------------------------------------------------------------------------
@@ -877,6 +903,9 @@ __global__ void __launch_bounds__(Geo<M>::NT, (region_min_blocks<T, M>()))
 moments_kernel(RegionArgs<T> a)
 {
     using G = Geo<M>;
+    // the compact form picks its sweep per warp, which is only legal without
+    // the per-plane barriers of the single-buffer sweep
+    static_assert(!G::CY || DB, "compact regions must keep both vectors in shared memory");
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* bufA = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[2][2][32];          // [step parity][d2, d1][warp]
@@ -928,9 +957,11 @@ moments_kernel(RegionArgs<T> a)
                 else nl_update<T, M, DB>(a, sc, sec, s);
                 __syncthreads();
             }
-            T aa, ab;
-            stencil_sweep<T, M, true, DB>(a, cur, sec, vwin, s, dshift, aa, ab,
-                                          &s_mom[i + 1]);
+            T aa, ab, unused;
+            if (G::CY && (warp < FD_NO || warp >= G::S - FD_NO))   // warp-uniform
+                stencil_sweep<T, M, true, DB, true>(a, cur, sec, vwin, s, dshift, aa, ab, unused, &s_mom[i + 1]);
+            else
+                stencil_sweep<T, M, true, DB, false>(a, cur, sec, vwin, s, dshift, aa, ab, unused, &s_mom[i + 1]);
             // t^{i+1}.t^{i+1} and t^{i+1}.t^i: column sums in T, warp trees, FP64 across warps
             const int par = i & 1;
             double w2 = warp_total(aa), w1 = warp_total(ab);
@@ -971,13 +1002,14 @@ __global__ void __launch_bounds__(Geo<M>::NT, (region_min_blocks<T, M>()))
 lanczos_kernel(RegionArgs<T> a)
 {
     using G = Geo<M>;
+    static_assert(!G::CY || DB, "compact regions must keep both vectors in shared memory");
     using SV = Sec<M, DB>;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
-    __shared__ double red_a[32], red_b[32];  // alpha and beta partials (separate: no reuse race)
+    __shared__ double red_a[32], red_b[32], red_c[32];  // v.w, w.w and v.v partials
     __shared__ int red_i[33];
     __shared__ T s_alpha, s_inv, s_bprev;
-    __shared__ int s_stop;
+    __shared__ int s_stop, s_explicit;
     __shared__ double s_dummy;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -1021,55 +1053,93 @@ lanczos_kernel(RegionArgs<T> a)
                 else nl_update<T, M, DB>(a, sc, sec, T(1));
                 __syncthreads();
             }
-            T aa, ab;
-            stencil_sweep<T, M, false, DB>(a, sm, sec, vwin, T(1), dshift, aa, ab,
-                                           &s_dummy);
-            double wt = warp_total(ab);
-            if (lane == 0) red_a[warp] = wt;
+            T ww, vw, vv;
+            if (G::CY && (warp < FD_NO || warp >= G::S - FD_NO))   // warp-uniform
+                stencil_sweep<T, M, false, DB, true>(a, sm, sec, vwin, T(1), dshift, ww, vw, vv, &s_dummy);
+            else
+                stencil_sweep<T, M, false, DB, false>(a, sm, sec, vwin, T(1), dshift, ww, vw, vv, &s_dummy);
+            // alpha = v.w and beta^2 = |w - alpha v|^2 = w.w - 2 alpha v.w + alpha^2 v.v from the
+            // sweep's sums, which saves a pass over w; where that difference cancels (beta below a
+            // tenth of |w|: near breakdown, e.g. tiny regions) beta is taken from w - alpha v itself
+            const double wa = warp_total(vw), wb = warp_total(ww), wc = warp_total(vv);
+            if (lane == 0) {
+                red_a[warp] = wa;
+                red_b[warp] = wb;
+                red_c[warp] = wc;
+            }
             __syncthreads();
             if (tid == 0) {
-                double al = 0.0;
-                for (int w = 0; w < G::NW; ++w) al += red_a[w];
+                double al = 0.0, w2 = 0.0, v2 = 0.0;
+                for (int w = 0; w < G::NW; ++w) {
+                    al += red_a[w];
+                    w2 += red_b[w];
+                    v2 += red_c[w];
+                }
                 alpha[it] = al;
-                s_alpha = (T)al;
                 if (fabs(al) + bprev > scale) scale = fabs(al) + bprev;
+                const double b2 = w2 - 2.0 * al * al + al * al * v2;
+                s_alpha = (T)al;
+                s_explicit = !(b2 > 0.01 * w2);
+                if (!s_explicit) {
+                    const double b = sqrt(b2);
+                    const int stop = (it == a.n_lanczos - 1) || (b <= 1e-10 * scale);
+                    if (!stop) beta[it] = b;
+                    else a.klen[node] = it + 1;
+                    s_stop = stop;
+                    s_inv = (T)(1.0 / b);
+                    s_bprev = (T)b;
+                    bprev = b;
+                }
             }
             __syncthreads();
-            // w -= alpha v ; beta = |w|
             const T alT = s_alpha;
-            T acc = 0;
-            if (active)
-                for (int z = 0; z < G::S; ++z) {
-                    T w = bcol[z * SV::ZS] - alT * col[z * G::PLANE];
-                    bcol[z * SV::ZS] = w;
-                    acc += w * w;
+            if (s_explicit) {                              // block-uniform
+                // w -= alpha v ; beta = |w|
+                T acc = 0;
+                if (active)
+                    for (int z = 0; z < G::S; ++z) {
+                        T w = bcol[z * SV::ZS] - alT * col[z * G::PLANE];
+                        bcol[z * SV::ZS] = w;
+                        acc += w * w;
+                    }
+                const double wt = warp_total(acc);
+                if (lane == 0) red_b[warp] = wt;
+                __syncthreads();
+                if (tid == 0) {
+                    double b2 = 0.0;
+                    for (int w = 0; w < G::NW; ++w) b2 += red_b[w];
+                    const double b = sqrt(b2);
+                    const int stop = (it == a.n_lanczos - 1) || (b <= 1e-10 * scale);
+                    if (!stop) beta[it] = b;
+                    else a.klen[node] = it + 1;
+                    s_stop = stop;
+                    s_inv = (T)(1.0 / b);
+                    s_bprev = (T)b;
+                    bprev = b;
                 }
-            wt = warp_total(acc);
-            if (lane == 0) red_b[warp] = wt;
-            __syncthreads();
-            if (tid == 0) {
-                double b2 = 0.0;
-                for (int w = 0; w < G::NW; ++w) b2 += red_b[w];
-                double b = sqrt(b2);
-                int stop = (it == a.n_lanczos - 1) || (b <= 1e-10 * scale);
-                if (!stop) beta[it] = b;
-                else a.klen[node] = it + 1;
-                s_stop = stop;
-                s_inv = (T)(1.0 / b);
-                s_bprev = (T)b;
-                bprev = b;
+                __syncthreads();
+                if (s_stop) break;
+                // sec <- beta v (the next step's beta_prev v_old), v <- w / beta
+                const T inv = s_inv, bT = s_bprev;
+                if (active)
+                    for (int z = 0; z < G::S; ++z) {
+                        T w = bcol[z * SV::ZS];
+                        T v = col[z * G::PLANE];
+                        bcol[z * SV::ZS] = bT * v;
+                        col[z * G::PLANE] = w * inv;
+                    }
+            } else {
+                if (s_stop) break;
+                // sec <- beta v, v <- (w - alpha v) / beta
+                const T inv = s_inv, bT = s_bprev;
+                if (active)
+                    for (int z = 0; z < G::S; ++z) {
+                        T w = bcol[z * SV::ZS];
+                        T v = col[z * G::PLANE];
+                        bcol[z * SV::ZS] = bT * v;
+                        col[z * G::PLANE] = (w - alT * v) * inv;
+                    }
             }
-            __syncthreads();
-            if (s_stop) break;
-            // sec <- beta v (the next step's beta_prev v_old), v <- w / beta
-            const T inv = s_inv, bT = s_bprev;
-            if (active)
-                for (int z = 0; z < G::S; ++z) {
-                    T w = bcol[z * SV::ZS];
-                    T v = col[z * G::PLANE];
-                    bcol[z * SV::ZS] = bT * v;
-                    col[z * G::PLANE] = w * inv;
-                }
             __syncthreads();
         }
         __syncthreads();
