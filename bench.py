@@ -74,6 +74,8 @@ def parse():
     p.add_argument("--history", type=int, default=16, help="scf_*: mixing history")
     p.add_argument("--beta", type=float, default=0.3, help="scf_*: mixing parameter")
     p.add_argument("--period", type=int, default=1, help="scf_*: Pulay period (1: Anderson every step)")
+    p.add_argument("--reuse-bounds", default="none",
+                   help="scf_*: w_max (Ha) -- reuse the last Lanczos bounds, widened by max|V - V_ref| <= w_max")
     return p.parse_args()
 
 
@@ -765,8 +767,9 @@ def run_scf(a):
     solver = SQSolver.from_workload(wl, s.positions, precision=prec, device=str(dev))
     V_loc = torch.from_numpy(s.V.ravel().copy()).to(dev)
     kerker = None if a.kerker == "none" else tuple(float(x) for x in a.kerker.split(","))
+    reuse = None if a.reuse_bounds == "none" else float(a.reuse_bounds)
     scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=a.beta, history=a.history, margin=wl.margin,
-                kerker=kerker, period=a.period)
+                kerker=kerker, period=a.period, reuse_bounds=reuse)
     solver.solve(V_loc, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)      # warm-up (not timed)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
@@ -791,8 +794,10 @@ def run_scf(a):
         "config": {"workload": f"{a.workload}: {wl.cells}^3 cells ({wl.n_atoms} atoms), {wl.n}^3 grid, "
                                f"{2 * wl.m + 1}^3 regions, n_pl={wl.npl}, kT={wl.kT}",
                    "mixing": {"beta": a.beta, "history": a.history, "period": a.period, "kerker": kerker},
+                   "reuse_bounds": reuse,
                    "tolerance": 1e-6, "parallelism": "single GPU"},
         "iterations": it, "converged": out["converged"], "residuals": [float(r) for r in out["residuals"]],
+        "lanczos_runs": out["lanczos_runs"],
         "poisson_iterations": out["poisson_iterations"], "wall_s": wall,
         "roofline": None, "e2e": None, "cpu_baseline": None, "gpu_launches": int(solver.launches - launches0),
         "clocks": clk,

@@ -288,6 +288,18 @@ void sq_batch_destroy(sq_batch *b);
  *   iters_host, rel_resid_host: HOST outputs (may be NULL).  SQ_ENOCONV if
  *   max_iter is reached first.  Allocates 4 N_d doubles of workspace in the
  *   context on first use.  Synchronises the stream.
+ * sq_widen_bounds(ctx, V, V_ref, chi_ref, zeta_ref, chi, zeta, w_host)
+ *   Spectral bounds of the nodal Hamiltonians of V from bounds computed for
+ *   V_ref, without a Lanczos run.  H_q(V) = H_q(V_ref) + diag(V - V_ref) on
+ *   the region, so (Weyl's inequality) every eigenvalue of H_q moves by at
+ *   most w = max_t |V(t) - V_ref(t)|: chi = chi_ref, zeta = zeta_ref + w
+ *   enclose the spectrum of H_q(V) wherever chi_ref +- zeta_ref enclose that
+ *   of H_q(V_ref) (Section 3.2 needs only an enclosing interval; a wider one
+ *   costs accuracy at a given n_pl, not correctness).  For an SCF loop whose
+ *   potential changes little between iterations.
+ *   V, V_ref, chi_ref, zeta_ref: device N_d FP64; chi, zeta: device N_d FP64
+ *   outputs (may be chi_ref, zeta_ref themselves); w_host: HOST output (may
+ *   be NULL).  Synchronises the stream; SQ_EINVAL if w is not finite.
  * sq_effective_potential(ctx, V_loc, phi, rho, alpha, V_out)
  *   V_out = V_loc + phi + v_x(rho), v_x = -(3 alpha / 2)(3 rho / pi)^(1/3)
  *   (Slater X-alpha; alpha = 2/3 is uniform-gas exchange; 0 where rho <= 0).
@@ -333,6 +345,8 @@ void sq_batch_destroy(sq_batch *b);
  * ------------------------------------------------------------------------- */
 int sq_poisson(sq_ctx *ctx, const double *rho, double *phi, double tol, int max_iter,
                int *iters_host, double *rel_resid_host);
+int sq_widen_bounds(sq_ctx *ctx, const double *V, const double *V_ref, const double *chi_ref,
+                    const double *zeta_ref, double *chi, double *zeta, double *w_host);
 int sq_effective_potential(sq_ctx *ctx, const double *V_loc, const double *phi, const double *rho,
                            double alpha, double *V_out);
 int sq_kerker(sq_ctx *ctx, const double *v_in, const double *v_out, double k0, double amin, double tol,

@@ -67,6 +67,12 @@ class SQSolver:
         sq.sq_spectral_bounds(self.ctx, V, self.chi, self.zeta, n_lanczos, margin)
         return self.chi, self.zeta
 
+    def widen_bounds(self, V, V_ref, chi_ref, zeta_ref):
+        """Bounds for V from bounds computed for V_ref, widened by w = max|V - V_ref|
+        (Weyl's inequality; sq_widen_bounds) into self.chi, self.zeta; returns w."""
+        sq.sq_set_stream(self.ctx)
+        return sq.sq_widen_bounds(self.ctx, V, V_ref, chi_ref, zeta_ref, self.chi, self.zeta)
+
     def compute_moments(self, V, chi=None, zeta=None):
         sq.sq_set_stream(self.ctx)
         sq.sq_moments(self.ctx, V, self.chi if chi is None else chi, self.zeta if zeta is None else zeta,
@@ -159,15 +165,25 @@ class SQSCF:
     sequences them."""
 
     def __init__(self, solver, V_loc, n_electrons, kT, alpha=2.0 / 3.0, beta=0.3, history=7, n_lanczos=40,
-                 margin=0.01, kerker=None, period=1):
+                 margin=0.01, kerker=None, period=1, reuse_bounds=None):
         """``kerker`` = (k0, amin): mix the Kerker-preconditioned residual
         (sq_kerker) in place of V_out - V_in; the stopping test stays on the
         unpreconditioned residual.  ``period`` = p > 1: Periodic Pulay
-        mixing (extrapolation on every p-th step, simple mixing between)."""
+        mixing (extrapolation on every p-th step, simple mixing between).
+        ``reuse_bounds`` = w_max (Ha): an iteration takes the Lanczos bounds
+        of the last potential V_ref they were computed for, widened by
+        w = max|V_in - V_ref| (sq_widen_bounds; by Weyl's inequality they
+        still enclose every nodal spectrum), instead of running Lanczos, as
+        long as w <= w_max.  Near convergence the bounds then stay fixed, so
+        the SQ map the mixer iterates no longer changes with the rounding of
+        fresh bounds (in FP32 that rounding moves zeta by ~1e-5 relative and
+        puts a floor under the residual); the fixed point is that of SQ with
+        those enclosing bounds, at most w_max wider than fresh ones."""
         torch = solver.torch
         self.solver, self.V_loc = solver, V_loc
         self.kerker = None if kerker is None else (float(kerker[0]), float(kerker[1]))
         self.period = int(period)
+        self.reuse = None if reuse_bounds is None else float(reuse_bounds)
         self.n_electrons, self.kT, self.alpha = float(n_electrons), float(kT), float(alpha)
         self.n_lanczos, self.margin = int(n_lanczos), float(margin)
         f64 = dict(dtype=torch.float64, device=solver.device)
@@ -200,8 +216,20 @@ class SQSCF:
         else:
             V_in.copy_(self.V_loc if V0 is None else V0)
         sq.sq_mixer_set_period(self.mixer, self.period, len(res))
+        ref = None                                   # (V_ref, chi_ref, zeta_ref) of the last Lanczos run
+        lanczos = 0
         for it in range(len(res), max_iter):
-            out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
+            widened = False
+            if self.reuse is not None and ref is not None:
+                w = sv.widen_bounds(V_in, *ref)
+                widened = w <= self.reuse
+            if widened:
+                out = sv.solve(V_in, self.n_electrons, self.kT, bounds=(sv.chi, sv.zeta))
+            else:
+                out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
+                lanczos += 1
+                if self.reuse is not None:
+                    ref = (V_in.clone(), sv.chi.clone(), sv.zeta.clone())
             if on_step is not None:
                 on_step(V_in, sv.rho, out["mu"])
             sq.sq_set_stream(sv.ctx)
@@ -217,14 +245,14 @@ class SQSCF:
             if res[-1] <= tol:
                 return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
                             n_elec=out["n_elec"], residuals=res, iterations=it + 1, converged=True,
-                            poisson_iterations=pit)
+                            poisson_iterations=pit, lanczos_runs=lanczos)
             V_in, V_next = V_next, V_in
             if checkpoint is not None:
                 X, F = sq.sq_mixer_export(self.mixer, sv.n_nodes)
                 np.savez(checkpoint, V=V_in.cpu().numpy(), X=X, F=F, residuals=np.array(res))
         return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
                     n_elec=out["n_elec"], residuals=res, iterations=max_iter, converged=False,
-                    poisson_iterations=pit)
+                    poisson_iterations=pit, lanczos_runs=lanczos)
 
     def close(self):
         if getattr(self, "mixer", None):

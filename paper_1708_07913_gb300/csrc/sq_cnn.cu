@@ -3,6 +3,7 @@
 // the forward pass, the backward pass and the Adam step (kernels in
 // sq_cnn.cuh).
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -12,6 +13,7 @@
 
 #include "../../include/sq.h"
 #include "sq_cnn.cuh"
+#include "sq_cnn_tc.cuh"
 
 using namespace sq;
 
@@ -65,6 +67,11 @@ struct sq_cnn {
     float* part = nullptr;
     double* lpart = nullptr;
     double* lout = nullptr;
+    // bfloat16 networks run the middle layer's forward on the tensor cores
+    // (sq_cnn_tc.cuh) unless SQ_CNN_TENSOR=0 was set when the network was
+    // created; its latched wait-expiry bit lives here
+    int tensor = 1;
+    unsigned* err = nullptr;
 };
 
 namespace {
@@ -121,9 +128,38 @@ int forward_t(sq_cnn* n, const CnnGrid& g, const double* V, double* rho)
     const int gN = grid_for(g.N, n->sm), gNC = grid_for(g.N * C, n->sm);
     cnn_input_kernel<T><<<gN, CNN_NT, 0, n->st>>>(g, V, n->v_shift + n->shift, n->v_scale, x0);
     cnn_conv_fwd_kernel<T, 1, 5><<<gNC, CNN_NT, 0, n->st>>>(g, x0, wt + OW1, n->w + OB1, n->z1, a1);
-    cnn_conv_fwd_kernel<T, C, 3><<<gNC, CNN_NT, 0, n->st>>>(g, a1, wt + OW2, n->w + OB2, n->z2, a2);
+    if constexpr (sizeof(T) == sizeof(Bf16)) {
+        if (n->tensor) {
+            static bool attr = false;        // the kernel's shared memory exceeds the 48 KB default
+            if (!attr) {
+                if (cudaFuncSetAttribute(cnn_conv2_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) !=
+                    cudaSuccess)
+                    return SQ_ECUDA;
+                attr = true;
+            }
+            const long long tiles = (g.N + TC_M - 1) / TC_M;
+            const int grid = (int)std::max<long long>(1, std::min<long long>(tiles, (long long)n->sm));
+            cnn_conv2_tc_kernel<<<grid, 128, TC_SMEM, n->st>>>(g, (const Bf16*)a1, (const Bf16*)(wt + OW2),
+                                                               n->w + OB2, n->z2, (Bf16*)a2, n->err);
+        } else {
+            cnn_conv_fwd_kernel<T, C, 3><<<gNC, CNN_NT, 0, n->st>>>(g, a1, wt + OW2, n->w + OB2, n->z2, a2);
+        }
+    } else {
+        cnn_conv_fwd_kernel<T, C, 3><<<gNC, CNN_NT, 0, n->st>>>(g, a1, wt + OW2, n->w + OB2, n->z2, a2);
+    }
     cnn_out_fwd_kernel<T><<<gN, CNN_NT, 0, n->st>>>(g, a2, wt + OW3, n->w + OB3, n->rho_scale, n->y, rho);
     return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;
+}
+
+// After a synchronisation: SQ_ETIMEOUT (and the bit cleared) if a tensor-core
+// wait expired since the last check.
+int take_tc_error(sq_cnn* n)
+{
+    unsigned e = 0;
+    if (cudaMemcpy(&e, n->err, sizeof(e), cudaMemcpyDeviceToHost) != cudaSuccess) return SQ_ECUDA;
+    if (!e) return SQ_OK;
+    if (cudaMemset(n->err, 0, sizeof(unsigned)) != cudaSuccess) return SQ_ECUDA;
+    return SQ_ETIMEOUT;
 }
 
 template <typename T>
@@ -245,11 +281,14 @@ int sq_cnn_create(sq_cnn** out, int channels, int bf16, void* cuda_stream)
     int rc;
     const size_t ts = bf16 ? sizeof(Bf16) : sizeof(float);
     if ((rc = alloc(&n->w, 4 * NPARAM)) || (rc = alloc(&n->g, 4 * NPARAM)) || (rc = alloc(&n->m, 4 * NPARAM)) ||
-        (rc = alloc(&n->v, 4 * NPARAM)) || (rc = alloc(&n->wt, ts * NPARAM))) {
+        (rc = alloc(&n->v, 4 * NPARAM)) || (rc = alloc(&n->wt, ts * NPARAM)) || (rc = alloc(&n->err, 4))) {
         sq_cnn_destroy(n);
         return rc;
     }
-    if (cudaMemsetAsync(n->g, 0, 4 * NPARAM, n->st) != cudaSuccess ||
+    const char* env = getenv("SQ_CNN_TENSOR");
+    n->tensor = !(env && strcmp(env, "0") == 0);
+    if (cudaMemsetAsync(n->err, 0, sizeof(unsigned), n->st) != cudaSuccess ||
+        cudaMemsetAsync(n->g, 0, 4 * NPARAM, n->st) != cudaSuccess ||
         cudaMemsetAsync(n->m, 0, 4 * NPARAM, n->st) != cudaSuccess ||
         cudaMemsetAsync(n->v, 0, 4 * NPARAM, n->st) != cudaSuccess || cudaStreamSynchronize(n->st) != cudaSuccess) {
         cudaGetLastError();
@@ -327,7 +366,7 @@ int sq_cnn_forward_sum(sq_cnn* n, int n1, int n2, int n3, const double* V, doubl
     if (cudaMemcpyAsync(sum_host, n->lout, sizeof(double), cudaMemcpyDeviceToHost, n->st) != cudaSuccess ||
         cudaStreamSynchronize(n->st) != cudaSuccess)
         return SQ_ECUDA;
-    return SQ_OK;
+    return take_tc_error(n);
 }
 
 int sq_cnn_backward(sq_cnn* n, int n1, int n2, int n3, const double* V, const double* rho_ref, double* rho,
@@ -348,6 +387,7 @@ int sq_cnn_backward(sq_cnn* n, int n1, int n2, int n3, const double* V, const do
         if (cudaMemcpyAsync(loss_host, n->lout, sizeof(double), cudaMemcpyDeviceToHost, n->st) != cudaSuccess ||
             cudaStreamSynchronize(n->st) != cudaSuccess)
             return SQ_ECUDA;
+        return take_tc_error(n);
     }
     return SQ_OK;
 }
@@ -371,7 +411,7 @@ void sq_cnn_destroy(sq_cnn* n)
     if (!n) return;
     if (n->st) cudaStreamSynchronize(n->st);
     free_bufs(n);
-    void* p[] = {n->w, n->g, n->m, n->v, n->wt};
+    void* p[] = {n->w, n->g, n->m, n->v, n->wt, n->err};
     for (void* q : p)
         if (q) cudaFree(q);
     delete n;

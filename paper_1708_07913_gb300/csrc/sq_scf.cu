@@ -62,6 +62,48 @@ __global__ void dot_kernel(const double* __restrict__ a1, const double* __restri
     }
 }
 
+// max over t of |a(t) - b(t)|, block maxima then the last block's maximum in
+// index order into *out (a maximum does not depend on the order; the form
+// matches dot_kernel).
+__global__ void maxabs_kernel(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                              double* partials, unsigned* counter, double* out)
+{
+    __shared__ double sh[T_RED / 32];
+    __shared__ bool last;
+    double s = 0.0;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x)
+        s = fmax(s, fabs(a[t] - b[t]));
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmax(m, sh[w]);
+        partials[blockIdx.x] = m;
+        __threadfence();
+        last = atomicAdd(counter, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (last && threadIdx.x == 0) {
+        __threadfence();
+        double m = 0.0;
+        for (unsigned k = 0; k < gridDim.x; ++k) m = fmax(m, ((volatile double*)partials)[k]);
+        *out = m;
+        *counter = 0;
+    }
+}
+
+// chi = chi_ref, zeta = zeta_ref + *w (the Weyl widening of sq_widen_bounds).
+__global__ void widen_kernel(const double* __restrict__ chi_ref, const double* __restrict__ zeta_ref,
+                             const double* w, double* chi, double* zeta, long long n)
+{
+    const double dw = *w;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+        chi[t] = chi_ref[t];
+        zeta[t] = zeta_ref[t] + dw;
+    }
+}
+
 // y = -lap_h x on the periodic grid (x fastest): the d = 0 term of
 // Eq. (FD:Laplacian) appears in its six axis terms.
 struct FDW {
@@ -434,6 +476,29 @@ int sq_poisson(sq_ctx* c, const double* rho, double* phi, double tol, int max_it
     if (iters_host) *iters_host = it;
     if (rel_resid_host) *rel_resid_host = bnorm > 0.0 ? sqrt(rr) / bnorm : 0.0;
     return (bnorm > 0.0 && sqrt(rr) > tol * bnorm) ? SQ_ENOCONV : SQ_OK;
+}
+
+int sq_widen_bounds(sq_ctx* c, const double* V, const double* V_ref, const double* chi_ref, const double* zeta_ref,
+                    double* chi, double* zeta, double* w_host)
+{
+    if (!c) return SQ_EINVAL;
+    if (!device_ptr(V) || !device_ptr(V_ref) || !device_ptr(chi_ref) || !device_ptr(zeta_ref) || !device_ptr(chi) ||
+        !device_ptr(zeta))
+        return SQ_EINVAL;
+    PoissonWS* ws = nullptr;
+    int rc = context_ws(c, &ws);
+    if (rc) return rc;
+    const long long n = c->g.Nd;
+    maxabs_kernel<<<ws->red.blocks, T_RED, 0, c->stream>>>(V, V_ref, n, ws->red.partials, ws->red.counter,
+                                                             ws->red.out);
+    widen_kernel<<<grid_for(n, c->sm_count), 256, 0, c->stream>>>(chi_ref, zeta_ref, ws->red.out, chi, zeta, n);
+    c->launches += 2;
+    if (cudaGetLastError() != cudaSuccess) return SQ_ECUDA;
+    double w = 0.0;
+    if ((rc = read_slot(ws->red, 0, &w, c->stream))) return rc;
+    if (!std::isfinite(w)) return SQ_EINVAL;
+    if (w_host) *w_host = w;
+    return SQ_OK;
 }
 
 int sq_effective_potential(sq_ctx* c, const double* V_loc, const double* phi, const double* rho, double alpha,

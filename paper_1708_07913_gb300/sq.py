@@ -24,7 +24,8 @@ SQ_FP64, SQ_FP32 = 0, 1
 EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments", "sq_fermi_level",
            "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
-           "sq_batch_destroy", "sq_poisson", "sq_effective_potential", "sq_mixer_create", "sq_mixer_step",
+           "sq_batch_destroy", "sq_poisson", "sq_widen_bounds", "sq_effective_potential", "sq_mixer_create",
+           "sq_mixer_step",
            "sq_mixer_set_period", "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
            "sq_nl_forces", "sq_nl_forces_nodes", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create",
            "sq_cnn_set_params", "sq_cnn_get_params", "sq_cnn_forward", "sq_cnn_set_shift", "sq_cnn_forward_sum",
@@ -80,6 +81,7 @@ def load(path: str = LIB_PATH):
         lib.sq_batch_destroy.restype = None
         lib.sq_poisson.argtypes = [vp, vp, vp, C.c_double, ip, C.POINTER(ip), dp]
         lib.sq_effective_potential.argtypes = [vp, vp, vp, vp, C.c_double, vp]
+        lib.sq_widen_bounds.argtypes = [vp, vp, vp, vp, vp, vp, vp, dp]
         lib.sq_nl_forces.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp]
         lib.sq_nl_forces_nodes.argtypes = [vp, vp, vp, vp, C.c_double, C.c_double, vp, C.c_longlong, vp]
         lib.sq_mixer_set_period.argtypes = [vp, ip, C.c_longlong]
@@ -275,6 +277,15 @@ def sq_poisson(ctx, rho, phi, tol=1e-12, max_iter=5000):
     _check(load().sq_poisson(C.c_void_p(ctx), _dptr(rho, "rho"), _dptr(phi, "phi"), float(tol), int(max_iter),
                              C.byref(it), C.byref(res)), "sq_poisson")
     return it.value, res.value
+
+
+def sq_widen_bounds(ctx, V, V_ref, chi_ref, zeta_ref, chi, zeta) -> float:
+    """chi = chi_ref, zeta = zeta_ref + w with w = max|V - V_ref| (Weyl enclosure); returns w."""
+    w = C.c_double()
+    _check(load().sq_widen_bounds(C.c_void_p(ctx), _dptr(V, "V"), _dptr(V_ref, "V_ref"), _dptr(chi_ref, "chi_ref"),
+                                  _dptr(zeta_ref, "zeta_ref"), _dptr(chi, "chi"), _dptr(zeta, "zeta"), C.byref(w)),
+           "sq_widen_bounds")
+    return w.value
 
 
 def sq_effective_potential(ctx, V_loc, phi, rho, alpha, V_out):

@@ -195,3 +195,32 @@ def test_full_size_gradient_is_the_derivative_of_the_loss():
     an = float(g @ (thetas[0] - thetas[1]))
     assert abs(fd) > 1e-6 and abs(an - fd) <= 1e-2 * abs(fd)
     sq.sq_cnn_destroy(net)
+
+
+@pytest.mark.parametrize("shape", [(16, 16, 16), (21, 20, 19)])
+def test_tensor_core_middle_layer(shape, monkeypatch):
+    """The bfloat16 network's 32 -> 32 layer on the tensor cores (tcgen05
+    implicit GEMM, FP32 accumulation in TMEM; the default) against the same
+    layer on CUDA cores (SQ_CNN_TENSOR=0) and against the oracle.  The two
+    GPU forms differ only in the order of the FP32 sums, so apart from
+    activations that round to a neighbouring bfloat16 value they agree; both
+    meet the oracle tolerance of the bfloat16 network.  Grids with a ragged
+    last 128-node tile (21 x 20 x 19 = 7980 nodes)."""
+    p, V, _ = _problem(shape, seed=7 + sum(shape))
+    rho = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("SQ_CNN_TENSOR", mode)
+        net = sq.sq_cnn_create(32, True)
+        sq.sq_cnn_set_params(net, _flat(p), p["v_shift"], p["v_scale"], p["rho_scale"])
+        out = torch.empty(V.size, dtype=torch.float64, device=DEV)
+        total = sq.sq_cnn_forward_sum(net, shape, _dev(V), out)       # synchronises and reports wait expiry
+        rho[mode] = out.cpu().numpy()
+        assert abs(total - rho[mode].sum()) < 1e-9 * abs(total)
+        sq.sq_cnn_destroy(net)
+    rho_o, _ = cnn.forward(p, V, bf16=True)
+    rho_o = rho_o.ravel()
+    for mode in ("1", "0"):
+        np.testing.assert_allclose(rho[mode], rho_o, rtol=0, atol=2e-3 * np.abs(rho_o).max())
+    d = rho["1"] - rho["0"]
+    assert np.abs(d).max() <= 2e-3 * np.abs(rho["0"]).max()
+    assert np.linalg.norm(d) <= 2e-4 * np.linalg.norm(rho["0"])

@@ -112,6 +112,41 @@ def test_scf_matches_oracle_scf():
     solver.close()
 
 
+def test_widen_bounds_and_scf_that_reuses_them():
+    """sq_widen_bounds: zeta grows by exactly max|V - V_ref| (chi unchanged),
+    and the widened bounds of a changed potential still enclose every nodal
+    spectrum (all moments in [-1, 1]).  An SCF that reuses widened bounds
+    (refreshed when the widening would pass 0.05 Ha) runs fewer Lanczos
+    steps, converges, and lands within the effect of that widening of the
+    plain SCF's fixed point (a wider interval changes the SQ approximation,
+    not its correctness)."""
+    wl = synth.custom_workload("scf8r", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1742)
+    s = synth.make_system(wl)
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    V = _dev(s.V)
+    chi0, zeta0 = (t.clone() for t in solver.bounds(V, wl.n_lanczos, wl.margin))
+    dV = 0.03 * np.cos(np.arange(wl.n_nodes) * 0.21)
+    V2 = V + _dev(dV)
+    w = solver.widen_bounds(V2, V, chi0, zeta0)
+    assert w == np.abs(V2.cpu().numpy() - V.cpu().numpy()).max()
+    assert torch.equal(solver.chi, chi0)
+    np.testing.assert_array_equal(solver.zeta.cpu().numpy(), zeta0.cpu().numpy() + w)
+    mom = solver.compute_moments(V2).cpu().numpy()
+    assert np.abs(mom).max() <= 1 + 1e-9
+    V_loc = _dev(s.V)
+    plain = SQSCF(solver, V_loc, wl.n_electrons, wl.kT).run(tol=1e-8, max_iter=60)
+    rho_plain = plain["rho"].cpu().numpy().copy()            # the solver's buffer, reused by the next run
+    reuse = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, reuse_bounds=0.05).run(tol=1e-8, max_iter=60)
+    assert plain["converged"] and reuse["converged"]
+    assert plain["lanczos_runs"] == plain["iterations"] and reuse["lanczos_runs"] < reuse["iterations"]
+    np.testing.assert_allclose(reuse["rho"].cpu().numpy(), rho_plain, atol=2e-3 * np.abs(rho_plain).max())
+    assert abs(reuse["mu"] - plain["mu"]) < 2e-3
+    print(f"SCF to 1e-8: plain {plain['iterations']} iterations ({plain['lanczos_runs']} Lanczos runs), "
+          f"reusing bounds {reuse['iterations']} ({reuse['lanczos_runs']} Lanczos runs)")
+    solver.close()
+
+
 def test_scf_checkpoint_and_resume(tmp_path):
     """An SCF stopped after 4 iterations and resumed from its checkpoint (the
     next input potential and the mixing history) takes the same iterations

@@ -36,6 +36,23 @@ def test_potential_shift_is_identity_shift():
     np.testing.assert_allclose(H2 - H1, c * np.eye(H1.shape[0]), atol=1e-12)
 
 
+def test_potential_change_moves_spectrum_within_its_max():
+    """Weyl's inequality for the nodal Hamiltonian: changing V by dV moves
+    every eigenvalue of H_q by at most max|dV| over the region, so bounds
+    widened by max|dV| still enclose the spectrum (the reading behind reusing
+    spectral bounds between SCF iterations).  Checked on dense H_q with
+    projectors for a smooth and a rough change."""
+    osys, pos, V, h = _small_system()
+    rng = np.random.default_rng(17)
+    for dV in (0.05 * np.sin(np.arange(V.size) * 0.37).reshape(V.shape), 0.2 * rng.standard_normal(V.shape)):
+        o2 = oracle.OracleSystem(V + dV, h, osys.m, pos, synth.projector_types(True))
+        for q in (0, 5, 17, 200):
+            e1 = np.linalg.eigvalsh(osys.dense_H(q))
+            e2 = np.linalg.eigvalsh(o2.dense_H(q))
+            assert np.abs(e2 - e1).max() <= np.abs(dV).max() * (1 + 1e-12) + 1e-12
+            assert e2.min() >= e1.min() - np.abs(dV).max() - 1e-12 and e2.max() <= e1.max() + np.abs(dV).max() + 1e-12
+
+
 def _nonlocal_spectrum(h, R, pt, m, n):
     """Non-zero eigenvalues of the region-restricted V_nl = H - H(no projectors)
     at the node (m+1, m+1, m+1).  V_nl has rank <= 4 per atom, so a random
