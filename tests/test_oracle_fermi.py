@@ -77,6 +77,33 @@ def test_periodic_mode_converges_to_dense_diagonalisation():
     assert abs(r["n_elec"] - Ne) < 1e-9 * Ne
 
 
+def test_periodic_mode_matches_dense_diagonalisation_at_16_cubed():
+    """al4_16's grid and potential (16^3, the 4096 x 4096 periodic H, kT 0.1,
+    12 electrons, no projectors).  mu from the dense spectrum; the periodic-
+    region SQ density at seeded nodes tends to (2/h^3) sum_n |psi_n(q)|^2
+    g(lambda_n) as the degree grows: the Chebyshev interpolant of g converges
+    geometrically, to rounding at n_pl = 800 on a spectrum ~47 Ha wide."""
+    s = synth.make_system("al4_16")
+    wl = s.wl
+    osys = oracle.OracleSystem(s.V, wl.h, 0, s.positions, (), periodic=True)
+    lam, vec = np.linalg.eigh(osys.dense_H(0))
+    assert lam.size == 4096
+    kT, Ne = wl.kT, wl.n_electrons
+    g = lambda mu: 1.0 / (1.0 + np.exp((lam - mu) / kT))  # noqa: E731
+    mu = brentq(lambda mu: 2 * g(mu).sum() - Ne, lam[0] - 50 * kT, lam[-1] + 50 * kT, xtol=1e-14)
+    nodes = synth.sample_nodes(wl.n_nodes, 6, seed=11)
+    exact = 2.0 / wl.h ** 3 * (vec[nodes] ** 2 @ g(mu))
+    chi, zeta = osys.bounds(nodes, 80, 0.01)
+    assert np.all(chi - zeta < lam[0]) and np.all(chi + zeta > lam[-1])       # the bounds enclose the spectrum
+    errs = []
+    for npl in (200, 400, 800):
+        W = oracle.cc_weights(osys.moments(nodes, chi, zeta, npl))
+        rho, *_ = oracle.density_energy(W, chi, zeta, mu, kT, wl.h)
+        errs.append(np.abs(rho - exact).max() / exact.max())
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[1] < 1e-6 and errs[2] < 1e-11
+
+
 def test_infinite_cell_density_matches_dense_nodal_matrix():
     """e_q^T g(H_q) e_q from the dense nodal matrix (same chi, zeta, mu)."""
     n = 16
