@@ -87,17 +87,18 @@ void ws_release(ForceWS* w)
 
 // Arguments and launch of the force kernel in precision T (the context's
 // recurrence precision), then the fixed-order sum over its CTAs.
-// Grid and dynamic shared memory of the force kernel in precision T: the
-// in-place form keeps the current recurrence vector (S^3 values) in shared
-// memory; SQ_FORCE_GLOBAL=1 in the environment selects the form with every
-// vector in global scratch (for comparisons).  The dynamic shared-memory
-// limit of the kernel is only ever raised.
+// Grid and dynamic shared memory of the force kernel in precision T.  By
+// default every recurrence vector is in per-CTA global scratch (it stays
+// L1/L2 resident and measured faster); SQ_FORCE_SMEM=1 in the environment
+// selects the in-place form, which keeps the current vector (S^3 values) in
+// shared memory.  The dynamic shared-memory limit of the kernel is only ever
+// raised.
 template <typename T>
 int force_config(sq_ctx* c, long long nq, bool* inplace, size_t* dyn, int* blocks)
 {
     const int S = 2 * c->g.m + 1;
-    const char* env = getenv("SQ_FORCE_GLOBAL");
-    *inplace = !(env && env[0] == '1');
+    const char* env = getenv("SQ_FORCE_SMEM");
+    *inplace = env && env[0] == '1';
     *dyn = *inplace ? sizeof(T) * (size_t)S * S * S : 0;
     const void* fn = *inplace ? (const void*)nl_force_kernel<T, true> : (const void*)nl_force_kernel<T, false>;
     cudaFuncAttributes fa;

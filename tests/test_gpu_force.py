@@ -66,9 +66,17 @@ CASES = {
 }
 
 
+@pytest.mark.parametrize("form", ["global", "smem"])
 @pytest.mark.parametrize("precision", [SQ_FP64, SQ_FP32])
 @pytest.mark.parametrize("name", list(CASES))
-def test_nl_forces_match_oracle(name, precision):
+def test_nl_forces_match_oracle(name, precision, form, monkeypatch):
+    """Both storage forms of the force kernel: every vector in global scratch
+    (the default), and the current vector in shared memory (SQ_FORCE_SMEM=1),
+    read by the library at each call."""
+    if form == "smem":
+        monkeypatch.setenv("SQ_FORCE_SMEM", "1")
+    else:
+        monkeypatch.delenv("SQ_FORCE_SMEM", raising=False)
     wl, s, pt = _system(**CASES[name])
     osys = oracle.OracleSystem(s.V, wl.h, wl.m, s.positions, pt)
     nodes = np.arange(wl.n_nodes)
@@ -86,15 +94,21 @@ def test_nl_forces_match_oracle(name, precision):
     solver.close()
 
 
-@pytest.mark.parametrize("name,precision,count", [("al108_48", SQ_FP64, 16), ("al108_48", SQ_FP32, 16),
-                                                  ("al2048_128", SQ_FP32, 6)])
-def test_nl_forces_full_size_sampled_nodes(name, precision, count):
+@pytest.mark.parametrize("name,precision,count,form", [("al108_48", SQ_FP64, 16, "global"),
+                                                       ("al108_48", SQ_FP32, 16, "global"),
+                                                       ("al108_48", SQ_FP32, 16, "smem"),
+                                                       ("al2048_128", SQ_FP32, 6, "global")])
+def test_nl_forces_full_size_sampled_nodes(name, precision, count, form, monkeypatch):
     """Full-size workloads: al108_48 (the benchmark workload: 25^3 regions,
     n_pl 48, 108 atoms) and al2048_128 (the scale workload: 128^3 grid, 29^3
     regions, n_pl 64, 2048 atoms; FP32, as FP64 regions stop at 25^3), s + 3p.
     The force contributions of seeded nodes on the benchmark's launch
     configuration, against the oracle on the same nodes (the oracle's bounds
     and Fermi level on the GPU side)."""
+    if form == "smem":
+        monkeypatch.setenv("SQ_FORCE_SMEM", "1")
+    else:
+        monkeypatch.delenv("SQ_FORCE_SMEM", raising=False)
     s = synth.make_system(name)
     wl = s.wl
     nodes = synth.sample_nodes(wl.n_nodes, count, seed=31)
