@@ -29,6 +29,7 @@ reports the total over ranks divided by the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import math
@@ -66,6 +67,11 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (nodes); 0 = automatic")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-context", action="store_true", help="skip the FP64-vs-FP32 comparison on al108_48")
+    p.add_argument("--refine-at", default="none",
+                   help="scf_*, warmstart_c4: residual at which an FP64 context takes over (none: FP32 throughout)")
+    p.add_argument("--batch-plan", choices=["auto", "streams", "share", "queue"], default="auto",
+                   help="batch16: launch plan (auto: the autotuner times them and keeps the fastest)")
+    p.add_argument("--nodes-per-item", type=int, default=1, help="batch16 with --batch-plan queue: nodes per work item")
     p.add_argument("--train-geometries", type=int, default=250, help="warmstart_c4: seeded training geometries")
     p.add_argument("--train-iters", type=int, default=8, help="warmstart_c4: SCF iterations kept per geometry")
     p.add_argument("--train-steps", type=int, default=1000, help="warmstart_c4: Adam steps")
@@ -511,7 +517,7 @@ def run_batch(a):
     systems, and the same systems run one after another through the
     single-system calls for comparison."""
     import torch
-    from paper_1708_07913_gb300 import SQ_FP32, SQBatch, SQSolver, build
+    from paper_1708_07913_gb300 import SQ_FP32, SQBatch, SQSolver, build, sq
 
     dev = torch.device("cuda:0")
     torch.cuda.set_device(dev)
@@ -539,6 +545,10 @@ def run_batch(a):
     torch.cuda.synchronize()
     t_seq = e0.elapsed_time(e1) / 1e3
     batch = SQBatch(solvers)
+    plans = {"auto": sq.SQ_BATCH_AUTO, "streams": sq.SQ_BATCH_STREAMS, "share": sq.SQ_BATCH_STREAMS_SHARE,
+             "queue": sq.SQ_BATCH_QUEUE}
+    if a.batch_plan != "auto":
+        batch.set_plan(plans[a.batch_plan], a.nodes_per_item)
     t0 = time.perf_counter()
     batch.run(Vs, Ne, kT, n_lz, margin)                      # first call: autotune + capture
     batch.results()
@@ -577,9 +587,17 @@ def run_batch(a):
     sm_max = peaks.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     peak = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    # kernels per system in one graph: potential copy, Lanczos, tridiagonal extremes, moments, weights,
-    # Fermi-state init, bracket, two end counts and 201 bisection counts, density
-    per_graph = len(wls) * (1 + 1 + 1 + 1 + 1 + 1 + 1 + 2 + 201 + 1)
+    plan, npi = batch.plan()
+    plan_name = {v: k for k, v in plans.items()}[plan]
+    # kernels per system in one graph: weights, Fermi-state init, bracket, two end counts and 201
+    # bisection counts, density, tridiagonal extremes; per system potential copy, Lanczos and moments
+    # (stream plans), or per group of systems with one region size a Lanczos and a moments queue kernel
+    post = len(wls) * (1 + 1 + 1 + 2 + 201 + 1 + 1)
+    if plan == sq.SQ_BATCH_QUEUE:
+        n_groups = sum(-(-c // 8) for c in collections.Counter(w.m for w in wls).values())
+        per_graph = post + 2 * n_groups
+    else:
+        per_graph = post + 3 * len(wls)
     line = {
         "metric": METRIC, "value": units / t, "unit": UNIT, "n_gpus": 1, "steps": a.steps, "warmup": a.warmup,
         "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
@@ -588,7 +606,11 @@ def run_batch(a):
             f"{w.cells}^3 cells {w.n}^3 grid h={w.h:.3f} {2 * w.m + 1}^3 regions n_pl={w.npl} kT={w.kT:.3f}"
             for w in wls),
             "precision": "FP32 recurrence/Lanczos vectors, FP64 moments, weights, Fermi level, energies",
-            "n_lanczos": n_lz, "margin": margin, "launch": "one CUDA graph per step, one stream per system",
+            "n_lanczos": n_lz, "margin": margin,
+            "launch": ("one CUDA graph per step: persistent queue kernels per group of systems with one region "
+                       f"size, {npi} node(s) per work item" if plan == sq.SQ_BATCH_QUEUE else
+                       "one CUDA graph per step, one stream per system"),
+            "plan": plan_name if a.batch_plan != "auto" else f"{plan_name} (autotuned)",
             "l2": "flushed between timed steps (256 MB write)", "parallelism": "single GPU"},
         "sequential_s": t_seq, "batch_speedup_vs_sequential": t_seq / t, "autotune_first_call_s": t_tune,
         "blocks_per_system": batch.blocks(),
@@ -717,8 +739,8 @@ def run_force(a):
                                f"a projector support",
                    "precision": ("FP32 recurrence, D and projector sums; FP64 coefficients and contraction"
                                  if prec == SQ_FP32 else "FP64 throughout"),
-                   "vector_storage": ("global scratch (SQ_FORCE_GLOBAL=1)" if os.environ.get("SQ_FORCE_GLOBAL") == "1"
-                                      else "current vector in shared memory"),
+                   "vector_storage": ("current vector in shared memory (SQ_FORCE_SMEM=1)"
+                                      if os.environ.get("SQ_FORCE_SMEM") == "1" else "global scratch"),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "single GPU"},
         "forces_max_abs": float(F.abs().max().item()),
@@ -768,18 +790,25 @@ def run_scf(a):
     V_loc = torch.from_numpy(s.V.ravel().copy()).to(dev)
     kerker = None if a.kerker == "none" else tuple(float(x) for x in a.kerker.split(","))
     reuse = None if a.reuse_bounds == "none" else float(a.reuse_bounds)
+    fine = None
+    refine_at = None if a.refine_at == "none" else float(a.refine_at)
+    if refine_at is not None:
+        fine = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=str(dev))
     scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=a.beta, history=a.history, margin=wl.margin,
-                kerker=kerker, period=a.period, reuse_bounds=reuse)
+                kerker=kerker, period=a.period, reuse_bounds=reuse,
+                refine=None if fine is None else (fine, refine_at))
     solver.solve(V_loc, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)      # warm-up (not timed)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
-    launches0 = solver.launches
+    launches0 = solver.launches + (fine.launches if fine is not None else 0)
     stream = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stamps = []
     t0 = time.perf_counter()
     e0.record(stream)
-    out = scf.run(tol=1e-6, max_iter=a.max_scf)
+    out = scf.run(tol=1e-6, max_iter=a.max_scf,
+                  on_step=lambda V, rho, mu: stamps.append(time.perf_counter()))
     e1.record(stream)
     torch.cuda.synchronize()
     wall = time.perf_counter() - t0
@@ -794,16 +823,20 @@ def run_scf(a):
         "config": {"workload": f"{a.workload}: {wl.cells}^3 cells ({wl.n_atoms} atoms), {wl.n}^3 grid, "
                                f"{2 * wl.m + 1}^3 regions, n_pl={wl.npl}, kT={wl.kT}",
                    "mixing": {"beta": a.beta, "history": a.history, "period": a.period, "kerker": kerker},
-                   "reuse_bounds": reuse,
+                   "reuse_bounds": reuse, "fp64_from_residual": refine_at,
                    "tolerance": 1e-6, "parallelism": "single GPU"},
         "iterations": it, "converged": out["converged"], "residuals": [float(r) for r in out["residuals"]],
-        "lanczos_runs": out["lanczos_runs"],
+        "lanczos_runs": out["lanczos_runs"], "fp64_from_iteration": out["refined_at"],
+        "iteration_wall_s": [b - a_ for a_, b in zip([t0] + stamps[:-1], stamps)],
         "poisson_iterations": out["poisson_iterations"], "wall_s": wall,
-        "roofline": None, "e2e": None, "cpu_baseline": None, "gpu_launches": int(solver.launches - launches0),
+        "roofline": None, "e2e": None, "cpu_baseline": None,
+        "gpu_launches": int(solver.launches + (fine.launches if fine is not None else 0) - launches0),
         "clocks": clk,
     }
     scf.close()
     solver.close()
+    if fine is not None:
+        fine.close()
     print(json.dumps(line), flush=True)
 
 
@@ -835,7 +868,10 @@ def run_warmstart(a):
         net = SQCNN(True, 0, *wsm.input_scales(use, fermi_referenced=fermi), device=str(dev))
         losses[label], t_train[label] = wsm.train(net, use, a.train_steps, fermi_referenced=fermi)
         nets[label] = (net, fermi)
-    res = wsm.compare(nets, target, tol=1e-6, max_iter=a.max_scf, device=str(dev))
+    reuse = None if a.reuse_bounds == "none" else float(a.reuse_bounds)
+    refine_at = None if a.refine_at == "none" else float(a.refine_at)
+    res = wsm.compare(nets, target, tol=1e-6, max_iter=a.max_scf, device=str(dev), reuse_bounds=reuse,
+                      refine_at=refine_at)
     clk = clocks.stop()
     for net, _ in nets.values():
         net.close()
@@ -852,6 +888,7 @@ def run_warmstart(a):
                    "fermi_level_offsets": [-0.1, -0.05, 0.0, 0.05, 0.1],
                    "scf_iterations_per_geometry": a.train_iters, "adam_steps": a.train_steps,
                    "mixing": "Anderson, history 16, beta 0.3, Kerker (0.5, 0.1)", "best": best,
+                   "reuse_bounds": reuse, "fp64_from_residual": refine_at,
                    "parallelism": "single GPU"},
         "plain_iterations": res["plain"]["iterations"], "plain_converged": res["plain"]["converged"],
         "results": res,

@@ -230,9 +230,9 @@ int sq_nl_forces_nodes(sq_ctx *ctx, const double *V, const double *chi, const do
  * counterpart for this.  A batch runs the whole step of the path -- spectral
  * bounds, moments, Fermi level and density/energies, as the single-system
  * calls above define them -- for every context in it as ONE CUDA graph
- * launch, each system on its own stream, so that systems of uneven size,
- * region and temperature share the GPU and the launch-bound Fermi-level
- * bisections of the systems overlap.
+ * launch, so that systems of uneven size, region and temperature share the
+ * GPU and the launch-bound Fermi-level bisections of the systems overlap.
+ * The contexts of a batch must be distinct.
  *
  * sq_batch_create(out, n, ctxs, cuda_stream)
  *   ctxs: HOST array of n >= 1 contexts, not owned (they must outlive the
@@ -244,20 +244,55 @@ int sq_nl_forces_nodes(sq_ctx *ctx, const double *V, const double *chi, const do
  *              margin)
  *   V, chi, zeta, moments, rho: HOST arrays of n DEVICE pointers, each with
  *   the layout of the single-system calls; n_electrons, kT: HOST arrays of n.
- *   Enqueues the step of every system and returns without waiting.  The
- *   first call tunes the launch (and so takes about two extra batch steps):
- *   two plans are timed as whole graphs -- every region kernel on its full
- *   persistent grid, and grids cut to SM shares proportional to each
- *   system's work (nodes x region points x steps) -- and the faster is kept.  A call whose pointers or parameters differ from
- *   the previous call's re-captures the graph (same plan).  Argument errors
- *   are SQ_EINVAL (checked on the host before anything is enqueued).
+ *   Enqueues the step of every system and returns without waiting.  Unless
+ *   sq_batch_set_plan fixed a plan, the first call tunes the launch (and so
+ *   takes about four extra batch steps): the plans below are timed as whole
+ *   graphs and the fastest is kept.  A call whose pointers or parameters
+ *   differ from the previous call's re-captures the graph (same plan).
+ *   Argument errors are SQ_EINVAL (checked on the host before anything is
+ *   enqueued).
+ *
+ * Launch plans:
+ *   SQ_BATCH_STREAMS        each system on its own stream, every region
+ *                           kernel on its full persistent grid;
+ *   SQ_BATCH_STREAMS_SHARE  the same with grids cut to SM shares
+ *                           proportional to each system's work (nodes x
+ *                           region points x steps);
+ *   SQ_BATCH_QUEUE          systems grouped by region half-width and
+ *                           precision (at most 8 per group); per group one
+ *                           persistent Lanczos kernel and one persistent
+ *                           moments kernel take work items from a device
+ *                           queue (one atomic add per item): slabs of each
+ *                           system's padded potential, then runs of
+ *                           nodes_per_item nodes.  A Lanczos item waits until
+ *                           its system's potential slabs are done: a bounded
+ *                           spin of at most the wait budget (SM clock cycles,
+ *                           default 2e9, about a second); when it runs out the
+ *                           item is skipped and the run's result is
+ *                           SQ_ETIMEOUT (from sq_batch_results).  Not
+ *                           available when a context uses the cluster form
+ *                           of the region kernels (SQ_EUNSUPPORTED).
+ * sq_batch_set_plan(b, plan, nodes_per_item)
+ *   SQ_BATCH_AUTO (the default: tune on the next run) or one of the plans
+ *   above, used as given; nodes_per_item in [1, 4096] for SQ_BATCH_QUEUE
+ *   (ignored otherwise).  Drops the captured graph.
+ * sq_batch_plan(b, plan, nodes_per_item): HOST ints receive the plan in use
+ *   (nodes_per_item 0 unless SQ_BATCH_QUEUE); SQ_EINVAL before the first run.
+ * sq_batch_set_wait(b, budget_cycles, wait_on_unset)
+ *   budget_cycles in [1, 1e12]: the queue plan's wait budget.
+ *   wait_on_unset = 1 makes every wait target one more potential slab than
+ *   exists, so every wait runs out (a test of the time-out path: the run
+ *   completes with SQ_ETIMEOUT and undefined results, and the batch and its
+ *   contexts stay usable); 0 restores normal waits.  Drops the captured
+ *   graph.
  * sq_batch_results(b, mu, e_band, e_ent, n_elec)
  *   Waits for the last run; HOST arrays of n (each may be NULL) receive each
  *   system's Fermi level, band energy, entropy energy and electron count
  *   (rho etc. are in the device arrays given to sq_batch_run).  Returns the
  *   first error of any system (SQ_ENOCONV, a latched device error, ...).
  * sq_batch_blocks(b, blocks): HOST array of n: the region-kernel grid chosen
- *   per system (0 = the full persistent grid); SQ_EINVAL before the first run.
+ *   per system (0 = the full persistent grid, and always 0 for the queue
+ *   plan); SQ_EINVAL before the first run.
  * sq_batch_destroy(b): releases the batch's streams and graph (NULL: no-op).
  * ------------------------------------------------------------------------- */
 typedef struct sq_batch sq_batch;
@@ -268,6 +303,15 @@ int sq_batch_run(sq_batch *b, const double *const *V, double *const *chi, double
 int sq_batch_results(sq_batch *b, double *mu_host, double *e_band_host, double *e_ent_host,
                      double *n_elec_host);
 int sq_batch_blocks(const sq_batch *b, int *blocks_host);
+enum {
+    SQ_BATCH_AUTO = -1,
+    SQ_BATCH_STREAMS = 0,
+    SQ_BATCH_STREAMS_SHARE = 1,
+    SQ_BATCH_QUEUE = 2
+};
+int sq_batch_set_plan(sq_batch *b, int plan, int nodes_per_item);
+int sq_batch_plan(const sq_batch *b, int *plan, int *nodes_per_item);
+int sq_batch_set_wait(sq_batch *b, long long budget_cycles, int wait_on_unset);
 void sq_batch_destroy(sq_batch *b);
 
 /* ---------------------------------------------------------------------------

@@ -123,8 +123,10 @@ class SQSolver:
 class SQBatch:
     """Several SQSolver systems run as one batch: the whole step (bounds,
     moments, Fermi level, density/energies) of every system is one CUDA graph
-    launch, each system on its own stream (sq_batch_* in include/sq.h).
-    Results land in each solver's own buffers (chi, zeta, moments, rho)."""
+    launch (sq_batch_* in include/sq.h): per-system streams, or persistent
+    queue kernels per group of systems with one region size, whichever the
+    autotuner measures faster unless a plan is set.  Results land in each
+    solver's own buffers (chi, zeta, moments, rho)."""
 
     def __init__(self, solvers):
         self.solvers = list(solvers)
@@ -144,6 +146,18 @@ class SQBatch:
     def blocks(self):
         """Region-kernel grid chosen per system by the autotuner (0 = the full persistent grid)."""
         return sq.sq_batch_blocks(self.batch, len(self.solvers))
+
+    def set_plan(self, plan, nodes_per_item=1):
+        """sq.SQ_BATCH_AUTO, SQ_BATCH_STREAMS, SQ_BATCH_STREAMS_SHARE or SQ_BATCH_QUEUE."""
+        sq.sq_batch_set_plan(self.batch, plan, nodes_per_item)
+
+    def plan(self):
+        """(plan, nodes_per_item) in use (after the first run)."""
+        return sq.sq_batch_plan(self.batch)
+
+    def set_wait(self, budget_cycles, wait_on_unset=False):
+        """Wait budget of the queue plan (SM clock cycles); wait_on_unset makes every wait run out."""
+        sq.sq_batch_set_wait(self.batch, budget_cycles, 1 if wait_on_unset else 0)
 
     def close(self):
         if getattr(self, "batch", None):
@@ -165,7 +179,7 @@ class SQSCF:
     sequences them."""
 
     def __init__(self, solver, V_loc, n_electrons, kT, alpha=2.0 / 3.0, beta=0.3, history=7, n_lanczos=40,
-                 margin=0.01, kerker=None, period=1, reuse_bounds=None):
+                 margin=0.01, kerker=None, period=1, reuse_bounds=None, refine=None):
         """``kerker`` = (k0, amin): mix the Kerker-preconditioned residual
         (sq_kerker) in place of V_out - V_in; the stopping test stays on the
         unpreconditioned residual.  ``period`` = p > 1: Periodic Pulay
@@ -178,12 +192,19 @@ class SQSCF:
         the SQ map the mixer iterates no longer changes with the rounding of
         fresh bounds (in FP32 that rounding moves zeta by ~1e-5 relative and
         puts a floor under the residual); the fixed point is that of SQ with
-        those enclosing bounds, at most w_max wider than fresh ones."""
+        those enclosing bounds, at most w_max wider than fresh ones.
+        ``refine`` = (solver_fp64, r_switch): once the residual is at or below
+        r_switch, the remaining iterations run on solver_fp64 (an FP64
+        context of the same grid and atoms), starting from the current bounds
+        and keeping the mixing history.  The FP32 recurrence leaves rounding
+        noise of ~1e-6 relative in the density, which stalls the residual
+        near that level; the FP64 iterations converge past it."""
         torch = solver.torch
         self.solver, self.V_loc = solver, V_loc
         self.kerker = None if kerker is None else (float(kerker[0]), float(kerker[1]))
         self.period = int(period)
         self.reuse = None if reuse_bounds is None else float(reuse_bounds)
+        self.refine = None if refine is None else (refine[0], float(refine[1]))
         self.n_electrons, self.kT, self.alpha = float(n_electrons), float(kT), float(alpha)
         self.n_lanczos, self.margin = int(n_lanczos), float(margin)
         f64 = dict(dtype=torch.float64, device=solver.device)
@@ -218,17 +239,25 @@ class SQSCF:
         sq.sq_mixer_set_period(self.mixer, self.period, len(res))
         ref = None                                   # (V_ref, chi_ref, zeta_ref) of the last Lanczos run
         lanczos = 0
+        refined_at = None
         for it in range(len(res), max_iter):
+            if self.refine is not None and refined_at is None and res and res[-1] <= self.refine[1]:
+                fine = self.refine[0]
+                fine.chi.copy_(sv.chi)
+                fine.zeta.copy_(sv.zeta)
+                sv, refined_at = fine, it
+                if ref is None:                      # without bound reuse: keep these bounds as the reference
+                    ref = (V_in.clone(), sv.chi.clone(), sv.zeta.clone())
             widened = False
-            if self.reuse is not None and ref is not None:
+            if ref is not None and (self.reuse is not None or refined_at is not None):
                 w = sv.widen_bounds(V_in, *ref)
-                widened = w <= self.reuse
+                widened = w <= (self.reuse if self.reuse is not None else 0.05)
             if widened:
                 out = sv.solve(V_in, self.n_electrons, self.kT, bounds=(sv.chi, sv.zeta))
             else:
                 out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
                 lanczos += 1
-                if self.reuse is not None:
+                if self.reuse is not None or refined_at is not None:
                     ref = (V_in.clone(), sv.chi.clone(), sv.zeta.clone())
             if on_step is not None:
                 on_step(V_in, sv.rho, out["mu"])
@@ -245,14 +274,14 @@ class SQSCF:
             if res[-1] <= tol:
                 return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
                             n_elec=out["n_elec"], residuals=res, iterations=it + 1, converged=True,
-                            poisson_iterations=pit, lanczos_runs=lanczos)
+                            poisson_iterations=pit, lanczos_runs=lanczos, refined_at=refined_at)
             V_in, V_next = V_next, V_in
             if checkpoint is not None:
                 X, F = sq.sq_mixer_export(self.mixer, sv.n_nodes)
                 np.savez(checkpoint, V=V_in.cpu().numpy(), X=X, F=F, residuals=np.array(res))
         return dict(V=V_in, rho=sv.rho, mu=out["mu"], e_band=out["e_band"], e_ent=out["e_ent"],
                     n_elec=out["n_elec"], residuals=res, iterations=max_iter, converged=False,
-                    poisson_iterations=pit, lanczos_runs=lanczos)
+                    poisson_iterations=pit, lanczos_runs=lanczos, refined_at=refined_at)
 
     def close(self):
         if getattr(self, "mixer", None):

@@ -15,7 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsq.so")
-SOURCES = ["sq_api.cu", "sq_kernels.cu", "sq_region_f32.cu", "sq_region_f64.cu", "sq_cluster_lo.cu", "sq_cluster_hi.cu",
+SOURCES = ["sq_api.cu", "sq_kernels.cu", "sq_region_f32.cu", "sq_region_f64.cu", "sq_queue_f32.cu", "sq_queue_f64.cu",
+           "sq_cluster_lo.cu", "sq_cluster_hi.cu",
            "sq_noalloc.cu", "sq_scf.cu",
            "sq_force.cu", "sq_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

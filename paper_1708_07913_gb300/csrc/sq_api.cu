@@ -10,7 +10,7 @@
 #include <new>
 #include <vector>
 
-#include "sq_region.cuh"
+#include "sq_queue.cuh"
 
 namespace sq {
 int region_config_f32(int m, int which, size_t extra, int* bps, size_t* smem);
@@ -22,6 +22,10 @@ int cluster_config_f32_lo(int m, int which, int ccap, int npl, int* clusters, si
 int cluster_config_f32_hi(int m, int which, int ccap, int npl, int* clusters, size_t* smem);
 int cluster_launch_f32_lo(int m, int which, const RegionArgs<float>& a, int clusters, size_t smem, cudaStream_t st);
 int cluster_launch_f32_hi(int m, int which, const RegionArgs<float>& a, int clusters, size_t smem, cudaStream_t st);
+int queue_config_f32(int m, int which, size_t extra, int* bps, size_t* smem);
+int queue_config_f64(int m, int which, size_t extra, int* bps, size_t* smem);
+int queue_launch_f32(int m, int which, const QueueArgs<float>& q, size_t extra, int blocks, cudaStream_t st);
+int queue_launch_f64(int m, int which, const QueueArgs<double>& q, size_t extra, int blocks, cudaStream_t st);
 }  // namespace sq
 
 using namespace sq;
@@ -97,6 +101,7 @@ int take_device_error(sq_ctx* c)
     unsigned z = 0;
     if (cudaMemcpyAsync(c->d_err, &z, sizeof(z), cudaMemcpyHostToDevice, c->stream) != cudaSuccess) return SQ_ECUDA;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+    if (e & ERR_TIMEOUT) return SQ_ETIMEOUT;
     if (e & ERR_NONFINITE) return SQ_EINVAL;
     if (e & ERR_CAPACITY) return SQ_ECAPACITY;
     return SQ_EBOUNDS;
@@ -401,6 +406,25 @@ struct sq_batch {
     int key_nl = 0;
     double key_margin = -1.0;
     std::vector<double> state;                   // host copy of the Fermi/energy states
+    // launch plan: requested (SQ_BATCH_AUTO: tuned on the first run) and in use
+    int plan_req = SQ_BATCH_AUTO, npi_req = 1;
+    int plan = SQ_BATCH_STREAMS, npi = 1;
+    long long wait_budget = 2000000000LL;        // SM cycles per queue wait (about a second)
+    int wait_unset = 0;
+    // queue plan: groups of systems with one region half-width and precision
+    struct Group {
+        int m = 0, prec = SQ_FP32;
+        std::vector<int> sys;                    // batch indices, at most QMAX
+        int bl = 0, bm = 0;                      // grids of the Lanczos and moments queue kernels
+        size_t xl = 0, xm = 0;                   // their dynamic shared memory beyond the region vectors
+        int off_l = 0, n_l = 0, off_m = 0, n_m = 0;   // item ranges in d_items
+        std::vector<int> need;                   // QI_VPAD items per system
+    };
+    std::vector<Group> groups;
+    int groups_npi = 0;                          // nodes per item the groups were built for (0: none)
+    QItem* d_items = nullptr;
+    unsigned* d_ctl = nullptr;                   // per group: 2 counters + QMAX completion counts
+    std::vector<cudaEvent_t> gfork;
 };
 
 namespace {
@@ -409,6 +433,19 @@ void batch_free_graph(sq_batch* b)
 {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
+}
+
+void batch_free_queue(sq_batch* b)
+{
+    if (b->d_items) cudaFree(b->d_items);
+    if (b->d_ctl) cudaFree(b->d_ctl);
+    b->d_items = nullptr;
+    b->d_ctl = nullptr;
+    for (cudaEvent_t e : b->gfork)
+        if (e) cudaEventDestroy(e);
+    b->gfork.clear();
+    b->groups.clear();
+    b->groups_npi = 0;
 }
 
 struct BatchArgs {
@@ -439,7 +476,7 @@ int batch_enqueue_one(sq_batch* b, int i, const BatchArgs& A, int bl, int bm)
 
 // Capture every system's step, each on its own stream forked from and
 // joined back into b->stream, and instantiate the graph.
-int batch_capture(sq_batch* b, const BatchArgs& A, const std::vector<int>& blocks, cudaGraphExec_t* out)
+int batch_capture_streams(sq_batch* b, const BatchArgs& A, const std::vector<int>& blocks, cudaGraphExec_t* out)
 {
     // grids first: nothing but stream work happens inside the capture
     std::vector<int> bl(b->n), bm(b->n);
@@ -478,6 +515,241 @@ int batch_capture(sq_batch* b, const BatchArgs& A, const std::vector<int>& block
     return rc;
 }
 
+// Projector supports covering a point (atom density x support volume): the
+// nonlocal share of a region point's arithmetic is about 8 flops per support
+// against ~52 for the local stencil.
+double proj_pairs(const sq_ctx* c)
+{
+    const double cell = (double)c->g.Nd * c->g.h * c->g.h * c->g.h;
+    return (c->has_s || c->has_p) ? c->n_atoms * (4.0 / 3.0) * M_PI * c->rnl * c->rnl * c->rnl / cell : 0.0;
+}
+
+// Per-CTA scratch for at least `blocks` CTAs (a queue kernel's grid can be
+// larger than the context's own, e.g. for a system with few nodes).
+// cudaFree synchronises the device, so no kernel still uses the old slices.
+int ensure_scratch(sq_ctx* c, int blocks)
+{
+    if (blocks <= c->grid_blocks) return SQ_OK;
+    void* p = nullptr;
+    int rc = dev_alloc(&p, c->scratch_bytes_per_cta * (size_t)blocks);
+    if (rc) return rc;
+    if (c->d_scratch) cudaFree(c->d_scratch);
+    c->d_scratch = p;
+    c->grid_blocks = blocks;
+    return SQ_OK;
+}
+
+// The queue plan is open to batches whose contexts all use the single-CTA
+// region kernels (the cluster kernels keep no per-CTA scratch).
+bool queue_available(const sq_batch* b)
+{
+    for (const sq_ctx* c : b->ctx)
+        if (c->cl_nc > 0 || !c->d_scratch) return false;
+    return true;
+}
+
+int queue_config(int prec, int m, int which, size_t extra, int* bps, size_t* smem)
+{
+    return prec == SQ_FP32 ? queue_config_f32(m, which, extra, bps, smem) : queue_config_f64(m, which, extra, bps, smem);
+}
+
+constexpr long long VPAD_CHUNK = 32768;          // padded-potential elements per QI_VPAD item
+
+// Groups (one region half-width and precision, at most QMAX systems each),
+// their grids, and the item lists of their Lanczos and moments queues, with
+// `npi` nodes per QI_NODES item.  Within a queue, the systems with the
+// costlier nodes come first, so the last items taken are the cheaper ones.
+int batch_build_queue(sq_batch* b, int npi)
+{
+    batch_free_graph(b);
+    batch_free_queue(b);
+    std::vector<sq_batch::Group> G;
+    for (int i = 0; i < b->n; ++i) {
+        const sq_ctx* c = b->ctx[i];
+        sq_batch::Group* g = nullptr;
+        for (auto& x : G)
+            if (x.m == c->g.m && x.prec == c->precision && (int)x.sys.size() < QMAX) g = &x;
+        if (!g) {
+            G.emplace_back();
+            g = &G.back();
+            g->m = c->g.m;
+            g->prec = c->precision;
+        }
+        g->sys.push_back(i);
+    }
+    std::vector<QItem> items;
+    for (auto& g : G) {
+        for (int i : g.sys) {
+            g.xl = std::max(g.xl, region_extra(b->ctx[i], 1));
+            g.xm = std::max(g.xm, region_extra(b->ctx[i], 0));
+        }
+        int bpl = 0, bpm = 0;
+        size_t sm = 0;
+        int rc;
+        if ((rc = queue_config(g.prec, g.m, 1, g.xl, &bpl, &sm)) || (rc = queue_config(g.prec, g.m, 0, g.xm, &bpm, &sm)))
+            return rc;
+        const int sms = b->ctx[g.sys[0]]->sm_count;
+        g.bl = bpl * sms;
+        g.bm = bpm * sms;
+        for (int i : g.sys)
+            if ((rc = ensure_scratch(b->ctx[i], std::max(g.bl, g.bm)))) return rc;
+        const int ns = (int)g.sys.size();
+        g.need.assign(ns, 0);
+        g.off_l = (int)items.size();
+        for (int k = 0; k < ns; ++k) {
+            const sq_ctx* c = b->ctx[g.sys[k]];
+            const long long P = (long long)c->g.P1 * c->g.P2 * (c->g.n3 + 2 * c->g.m);
+            for (long long e0 = 0; e0 < P; e0 += VPAD_CHUNK) {
+                items.push_back({k, QI_VPAD, e0, std::min(P, e0 + VPAD_CHUNK)});
+                ++g.need[k];
+            }
+        }
+        for (int which = 1; which >= 0; --which) {
+            if (which == 0) g.off_m = (int)items.size();
+            std::vector<int> order(ns);
+            for (int k = 0; k < ns; ++k) order[k] = k;
+            auto cost = [&](int k) {                                 // per node, up to a common factor
+                const sq_ctx* c = b->ctx[g.sys[k]];
+                return (which == 1 ? 1.0 : (double)c->npl) * (1.0 + proj_pairs(c) * 8.0 / 52.0);
+            };
+            std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+            for (int k : order) {
+                const long long Nd = b->ctx[g.sys[k]]->g.Nd;
+                for (long long n0 = 0; n0 < Nd; n0 += npi) items.push_back({k, QI_NODES, n0, std::min(Nd, n0 + npi)});
+            }
+            if (which == 1) g.n_l = (int)items.size() - g.off_l;
+            else g.n_m = (int)items.size() - g.off_m;
+        }
+    }
+    int rc;
+    if ((rc = dev_alloc(&b->d_items, sizeof(QItem) * items.size())) ||
+        (rc = dev_alloc(&b->d_ctl, sizeof(unsigned) * (2 + QMAX) * G.size())))
+        return rc;
+    if (cudaMemcpy(b->d_items, items.data(), sizeof(QItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        return SQ_ECUDA;
+    }
+    b->gfork.assign(G.size(), nullptr);
+    for (auto& e : b->gfork)
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return SQ_ECUDA;
+        }
+    b->groups = std::move(G);
+    b->groups_npi = npi;
+    return SQ_OK;
+}
+
+int queue_launch(int m, int which, const QueueArgs<float>& q, size_t extra, int blocks, cudaStream_t st)
+{
+    return queue_launch_f32(m, which, q, extra, blocks, st);
+}
+int queue_launch(int m, int which, const QueueArgs<double>& q, size_t extra, int blocks, cudaStream_t st)
+{
+    return queue_launch_f64(m, which, q, extra, blocks, st);
+}
+
+// Enqueue group gi of the queue plan on b->own: the Lanczos queue (QI_VPAD
+// items, then the nodes), the tridiagonal extremes of its systems, the
+// moments queue; then fork each system's Fermi search and density onto its
+// own stream (joined at the end of the graph).
+template <typename T>
+int batch_enqueue_group(sq_batch* b, int gi, const BatchArgs& A)
+{
+    const sq_batch::Group& g = b->groups[gi];
+    const int ns = (int)g.sys.size();
+    unsigned* ctl = b->d_ctl + (size_t)gi * (2 + QMAX);
+    QueueArgs<T> q;
+    memset(&q, 0, sizeof(q));
+    for (int k = 0; k < ns; ++k) {
+        sq_ctx* c = b->ctx[g.sys[k]];
+        RegionArgs<T> a = region_args<T>(c);
+        a.n_lanczos = A.n_lanczos; a.nl_cap = c->nl_cap; a.alpha = c->d_alpha; a.beta = c->d_beta; a.klen = c->d_klen;
+        q.sys[k] = a;
+        q.V[k] = A.V[g.sys[k]];
+        q.need[k] = g.need[k];
+    }
+    q.items = b->d_items + g.off_l;
+    q.n_items = g.n_l;
+    q.next = ctl;
+    q.done = ctl + 2;
+    q.budget = b->wait_budget;
+    q.unset = b->wait_unset;
+    int rc = queue_launch(g.m, 1, q, g.xl, g.bl, b->own);
+    if (rc) return rc;
+    for (int k = 0; k < ns; ++k) {
+        sq_ctx* c = b->ctx[g.sys[k]];
+        c->launches++;
+        c->stream = b->own;
+        if ((rc = launch_tridiag_bounds(c, A.margin, A.chi[g.sys[k]], A.zeta[g.sys[k]]))) return rc;
+    }
+    for (int k = 0; k < ns; ++k) {
+        sq_ctx* c = b->ctx[g.sys[k]];
+        RegionArgs<T> a = region_args<T>(c);
+        const int i = g.sys[k];
+        a.chi = A.chi[i]; a.zeta = A.zeta[i]; a.moments = A.moments[i];
+        q.sys[k] = a;
+    }
+    q.items = b->d_items + g.off_m;
+    q.n_items = g.n_m;
+    q.next = ctl + 1;
+    rc = queue_launch(g.m, 0, q, g.xm, g.bm, b->own);
+    if (rc) return rc;
+    if (cudaEventRecord(b->gfork[gi], b->own) != cudaSuccess) return SQ_ECUDA;
+    for (int k = 0; k < ns; ++k) {
+        const int i = g.sys[k];
+        sq_ctx* c = b->ctx[i];
+        c->launches++;
+        c->stream = b->st[i];
+        if (cudaStreamWaitEvent(b->st[i], b->gfork[gi], 0) != cudaSuccess) return SQ_ECUDA;
+        if ((rc = launch_weights(c, A.moments[i]))) return rc;
+        if ((rc = enqueue_fermi(c, A.chi[i], A.zeta[i], A.Ne[i], A.kT[i]))) return rc;
+        if ((rc = enqueue_density(c, A.chi[i], A.zeta[i], 0.0, A.kT[i], A.rho[i], 1))) return rc;
+        if (cudaEventRecord(b->join[i], b->st[i]) != cudaSuccess) return SQ_ECUDA;
+    }
+    return SQ_OK;
+}
+
+// Capture the queue plan: the counters cleared, the groups one after another
+// on the batch's stream, every system's post-processing joined at the end.
+int batch_capture_queue(sq_batch* b, const BatchArgs& A, cudaGraphExec_t* out)
+{
+    std::vector<cudaStream_t> saved(b->n);
+    for (int i = 0; i < b->n; ++i) saved[i] = b->ctx[i]->stream;
+    if (cudaStreamBeginCapture(b->own, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return SQ_ECUDA;
+    }
+    int rc = SQ_OK;
+    if (cudaMemsetAsync(b->d_ctl, 0, sizeof(unsigned) * (2 + QMAX) * b->groups.size(), b->own) != cudaSuccess)
+        rc = SQ_ECUDA;
+    for (int gi = 0; gi < (int)b->groups.size() && rc == SQ_OK; ++gi)
+        rc = b->groups[gi].prec == SQ_FP32 ? batch_enqueue_group<float>(b, gi, A) : batch_enqueue_group<double>(b, gi, A);
+    for (int i = 0; i < b->n && rc == SQ_OK; ++i)
+        if (cudaStreamWaitEvent(b->own, b->join[i], 0) != cudaSuccess) rc = SQ_ECUDA;
+    for (int i = 0; i < b->n; ++i) b->ctx[i]->stream = saved[i];
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->own, &graph);
+    if (rc == SQ_OK && e != cudaSuccess) rc = SQ_ECUDA;
+    if (rc == SQ_OK && cudaGraphInstantiate(out, graph, 0) != cudaSuccess) rc = SQ_ECUDA;
+    if (graph) cudaGraphDestroy(graph);
+    if (rc) cudaGetLastError();
+    return rc;
+}
+
+// Capture launch plan `kind` (SQ_BATCH_STREAMS / _STREAMS_SHARE with the
+// per-system grids `blocks`, or SQ_BATCH_QUEUE with `npi` nodes per item).
+int batch_capture(sq_batch* b, const BatchArgs& A, int kind, const std::vector<int>& blocks, int npi,
+                  cudaGraphExec_t* out)
+{
+    if (kind != SQ_BATCH_QUEUE) return batch_capture_streams(b, A, blocks, out);
+    if (b->groups_npi != npi) {
+        const int rc = batch_build_queue(b, npi);
+        if (rc) return rc;
+    }
+    return batch_capture_queue(b, A, out);
+}
+
 // Time one launch of an instantiated graph.
 int batch_time(sq_batch* b, cudaGraphExec_t g, float* ms)
 {
@@ -494,14 +766,9 @@ int batch_time(sq_batch* b, cudaGraphExec_t g, float* ms)
     return rc;
 }
 
-// The autotuner.  Two launch plans are timed as complete graphs: every
-// region kernel on its full persistent grid (the systems' region kernels
-// queue for the SMs, and the small Fermi and density launches of a finished
-// system overlap the next), and grids cut to SM shares proportional to each
-// system's work (all systems side by side); the faster plan is kept.  Work
-// per system = nodes x region points x (n_lanczos + n_pl/2) x (1 + the
-// projector share of a point's arithmetic).
-int batch_tune(sq_batch* b, const BatchArgs& A)
+// Region-kernel grids cut to SM shares proportional to each system's work:
+// nodes x region points x (n_lanczos + n_pl/2) x (1 + the projector share).
+int share_blocks(sq_batch* b, const BatchArgs& A, std::vector<int>* share)
 {
     const int n = b->n;
     std::vector<double> w(n, 0.0);
@@ -509,38 +776,75 @@ int batch_tune(sq_batch* b, const BatchArgs& A)
     for (int i = 0; i < n; ++i) {
         const sq_ctx* c = b->ctx[i];
         const double S = 2.0 * c->g.m + 1.0;
-        // projector supports covering a point (atom density x support volume),
-        // at ~8 flops each against ~52 for the local stencil
-        const double cell = (double)c->g.Nd * c->g.h * c->g.h * c->g.h;
-        const double pairs = (c->has_s || c->has_p) ? c->n_atoms * (4.0 / 3.0) * M_PI * c->rnl * c->rnl * c->rnl / cell
-                                                    : 0.0;
-        w[i] = (double)c->g.Nd * S * S * S * (A.n_lanczos + c->npl / 2) * (1.0 + pairs * 8.0 / 52.0);
+        w[i] = (double)c->g.Nd * S * S * S * (A.n_lanczos + c->npl / 2) * (1.0 + proj_pairs(c) * 8.0 / 52.0);
         W += w[i];
     }
-    std::vector<int> full(n, 0), share(n, 1);
+    share->assign(n, 1);
     for (int i = 0; i < n; ++i) {
         int bm = 0;
         int rc = region_blocks(b->ctx[i], 0, &bm);
         if (rc) return rc;
         const int per_sm = std::max(1, bm / std::max(1, b->ctx[i]->sm_count));
-        share[i] = std::max(1, (int)std::floor(w[i] / W * b->ctx[i]->sm_count * per_sm));
+        (*share)[i] = std::max(1, (int)std::floor(w[i] / W * b->ctx[i]->sm_count * per_sm));
+    }
+    return SQ_OK;
+}
+
+// The autotuner.  Candidate plans are timed as complete graphs on the first
+// run and the fastest is kept:
+//   SQ_BATCH_STREAMS        every system on its own stream, each region kernel
+//                           on its full persistent grid (the systems' kernels
+//                           queue for the SMs; small Fermi and density
+//                           launches of a finished system overlap the next);
+//   SQ_BATCH_STREAMS_SHARE  the same with grids cut to SM shares proportional
+//                           to each system's work (systems side by side);
+//   SQ_BATCH_QUEUE          persistent queue kernels per group of systems with
+//                           one region size, with 1 or 4 nodes per item.
+// A plan set with sq_batch_set_plan is used as given.  Thread-block clusters
+// are not among the candidates: the cluster form of the region kernels is
+// slower on every region size measured.
+int batch_tune(sq_batch* b, const BatchArgs& A)
+{
+    const int n = b->n;
+    std::vector<int> full(n, 0), share;
+    int rc = share_blocks(b, A, &share);
+    if (rc) return rc;
+    struct Cand { int kind; int npi; };
+    std::vector<Cand> cands;
+    if (b->plan_req != SQ_BATCH_AUTO) {
+        cands.push_back({b->plan_req, b->npi_req});
+    } else {
+        cands.push_back({SQ_BATCH_STREAMS, 1});
+        cands.push_back({SQ_BATCH_STREAMS_SHARE, 1});
+        if (queue_available(b)) {
+            cands.push_back({SQ_BATCH_QUEUE, 1});
+            cands.push_back({SQ_BATCH_QUEUE, 4});
+        }
+    }
+    if (cands.size() == 1) {
+        b->plan = cands[0].kind;
+        b->npi = cands[0].npi;
+        b->blocks = b->plan == SQ_BATCH_STREAMS_SHARE ? share : full;
+        b->tuned = true;
+        return SQ_OK;
     }
     float best = 0.f;
-    std::vector<int> pick = full;
-    for (int plan = 0; plan < 2; ++plan) {
-        const std::vector<int>& bl = plan == 0 ? full : share;
+    int pick = 0;
+    for (size_t k = 0; k < cands.size(); ++k) {
         cudaGraphExec_t g = nullptr;
-        int rc = batch_capture(b, A, bl, &g);
+        rc = batch_capture(b, A, cands[k].kind, cands[k].kind == SQ_BATCH_STREAMS_SHARE ? share : full, cands[k].npi, &g);
         float ms = 0.f;
         if (rc == SQ_OK) rc = batch_time(b, g, &ms);
         if (g) cudaGraphExecDestroy(g);
         if (rc) return rc;
-        if (plan == 0 || ms < best) {
+        if (k == 0 || ms < best) {
             best = ms;
-            pick = bl;
+            pick = (int)k;
         }
     }
-    b->blocks = pick;
+    b->plan = cands[pick].kind;
+    b->npi = cands[pick].npi;
+    b->blocks = b->plan == SQ_BATCH_STREAMS_SHARE ? share : full;
     b->tuned = true;
     return SQ_OK;
 }
@@ -813,7 +1117,7 @@ int sq_batch_run(sq_batch* b, const double* const* V, double* const* chi, double
         batch_free_graph(b);
         int rc = SQ_OK;
         if (!b->tuned) rc = batch_tune(b, A);
-        if (rc == SQ_OK) rc = batch_capture(b, A, b->blocks, &b->exec);
+        if (rc == SQ_OK) rc = batch_capture(b, A, b->plan, b->blocks, b->npi, &b->exec);
         if (rc) {
             b->exec = nullptr;
             return rc;
@@ -863,10 +1167,43 @@ int sq_batch_blocks(const sq_batch* b, int* blocks_host)
     return b->tuned ? SQ_OK : SQ_EINVAL;
 }
 
+int sq_batch_set_plan(sq_batch* b, int plan, int nodes_per_item)
+{
+    if (!b) return SQ_EINVAL;
+    if (plan != SQ_BATCH_AUTO && plan != SQ_BATCH_STREAMS && plan != SQ_BATCH_STREAMS_SHARE && plan != SQ_BATCH_QUEUE)
+        return SQ_EINVAL;
+    if (plan == SQ_BATCH_QUEUE && (nodes_per_item < 1 || nodes_per_item > 4096)) return SQ_EINVAL;
+    if (plan == SQ_BATCH_QUEUE && !queue_available(b)) return SQ_EUNSUPPORTED;
+    batch_free_graph(b);
+    b->plan_req = plan;
+    b->npi_req = plan == SQ_BATCH_QUEUE ? nodes_per_item : 1;
+    b->tuned = false;
+    return SQ_OK;
+}
+
+int sq_batch_plan(const sq_batch* b, int* plan, int* nodes_per_item)
+{
+    if (!b || !plan || !nodes_per_item || !b->tuned) return SQ_EINVAL;
+    *plan = b->plan;
+    *nodes_per_item = b->plan == SQ_BATCH_QUEUE ? b->npi : 0;
+    return SQ_OK;
+}
+
+int sq_batch_set_wait(sq_batch* b, long long budget_cycles, int wait_on_unset)
+{
+    if (!b || budget_cycles < 1 || budget_cycles > 1000000000000LL || (wait_on_unset != 0 && wait_on_unset != 1))
+        return SQ_EINVAL;
+    batch_free_graph(b);
+    b->wait_budget = budget_cycles;
+    b->wait_unset = wait_on_unset;
+    return SQ_OK;
+}
+
 void sq_batch_destroy(sq_batch* b)
 {
     if (!b) return;
     batch_free_graph(b);
+    batch_free_queue(b);
     for (cudaStream_t s : b->st)
         if (s) cudaStreamDestroy(s);
     for (cudaEvent_t e : b->join)

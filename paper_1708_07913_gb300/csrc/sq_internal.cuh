@@ -33,6 +33,7 @@ constexpr int STAGE = 16;            // row entries staged per warp at a time in
 constexpr unsigned ERR_BOUNDS = 1u;
 constexpr unsigned ERR_CAPACITY = 2u;
 constexpr unsigned ERR_NONFINITE = 4u;   // a potential value that is NaN or infinite
+constexpr unsigned ERR_TIMEOUT = 8u;     // a bounded device wait ran out of its budget
 
 struct AtomTab {                     // per-atom projector geometry (device)
     int lo[3];
@@ -103,6 +104,26 @@ struct GridParams {
     double h;
     double w[FD_NO + 1];             // FD weights of Eq. (FD:Laplacian)
 };
+
+// One element of the potential with its periodic halo (Section 3.1, the
+// periodic index map): padded index t of (n1+2m) x (n2+2m) x (n3+2m), x fastest,
+// takes V at ((i-m) mod n1, (j-m) mod n2, (k-m) mod n3).  A non-finite value
+// latches ERR_NONFINITE.
+template <typename T>
+__device__ inline void vpad_elem(const double* __restrict__ V, T* __restrict__ Vp, int n1, int n2, int n3, int m,
+                                 long long t, unsigned* err)
+{
+    const int P1 = n1 + 2 * m, P2 = n2 + 2 * m;
+    const int i = (int)(t % P1);
+    const int j = (int)((t / P1) % P2);
+    const int k = (int)(t / ((long long)P1 * P2));
+    const int a = ((i - m) % n1 + n1) % n1;
+    const int b = ((j - m) % n2 + n2) % n2;
+    const int c = ((k - m) % n3 + n3) % n3;
+    const double v = V[a + (long long)n1 * (b + (long long)n2 * c)];
+    if (!isfinite(v)) atomicOr(err, ERR_NONFINITE);
+    Vp[t] = (T)v;
+}
 
 }  // namespace sq
 

@@ -21,20 +21,10 @@ template <typename T>
 __global__ void vpad_kernel(const double* __restrict__ V, T* __restrict__ Vp, int n1, int n2, int n3, int m,
                             unsigned* err)
 {
-    const int P1 = n1 + 2 * m, P2 = n2 + 2 * m, P3 = n3 + 2 * m;
-    const long long tot = (long long)P1 * P2 * P3;
+    const long long tot = (long long)(n1 + 2 * m) * (n2 + 2 * m) * (n3 + 2 * m);
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-         t += (long long)gridDim.x * blockDim.x) {
-        int i = (int)(t % P1);
-        int j = (int)((t / P1) % P2);
-        int k = (int)(t / ((long long)P1 * P2));
-        int a = ((i - m) % n1 + n1) % n1;
-        int b = ((j - m) % n2 + n2) % n2;
-        int c = ((k - m) % n3 + n3) % n3;
-        const double v = V[a + (long long)n1 * (b + (long long)n2 * c)];
-        if (!isfinite(v)) atomicOr(err, ERR_NONFINITE);
-        Vp[t] = (T)v;
-    }
+         t += (long long)gridDim.x * blockDim.x)
+        vpad_elem<T>(V, Vp, n1, n2, n3, m, t, err);
 }
 
 int launch_build_vpad(sq_ctx* ctx, const double* V)

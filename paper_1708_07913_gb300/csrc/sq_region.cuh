@@ -899,14 +899,12 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
 // Chebyshev moments kernel (Section 3.2, Eqs. Rec:FD and rhoqj).
 // ------------------------------------------------------------------------
 template <typename T, int M, bool DB>
-__global__ void __launch_bounds__(Geo<M>::NT, (region_min_blocks<T, M>()))
-moments_kernel(RegionArgs<T> a)
+__device__ void moments_node(const RegionArgs<T>& a, unsigned char* smem_raw, long long node)
 {
     using G = Geo<M>;
     // the compact form picks its sweep per warp, which is only legal without
     // the per-plane barriers of the single-buffer sweep
     static_assert(!G::CY || DB, "compact regions must keep both vectors in shared memory");
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* bufA = reinterpret_cast<T*>(smem_raw);
     __shared__ double red[2][2][32];          // [step parity][d2, d1][warp]
     __shared__ int red_i[33];
@@ -922,71 +920,77 @@ moments_kernel(RegionArgs<T> a)
     const int half = a.npl / 2;
     const bool has_nl = a.nl.n_atoms > 0;
 
-    for (long long node = blockIdx.x; node < a.g.Nd; node += gridDim.x) {
-        const int qi = (int)(node % a.g.n1);
-        const int qj = (int)((node / a.g.n1) % a.g.n2);
-        const int qk = (int)(node / ((long long)a.g.n1 * a.g.n2));
-        const double chi = a.chi[node], zeta = a.zeta[node];
-        const T dshift = (T)(-3.0 * a.g.w[0] - chi);
-        const T s1 = (T)(1.0 / zeta), s2 = (T)(2.0 / zeta);
-        const T* vwin = a.Vp + ((size_t)qk * a.g.P2 + qj) * a.g.P1 + qi;
+    const int qi = (int)(node % a.g.n1);
+    const int qj = (int)((node / a.g.n1) % a.g.n2);
+    const int qk = (int)(node / ((long long)a.g.n1 * a.g.n2));
+    const double chi = a.chi[node], zeta = a.zeta[node];
+    const T dshift = (T)(-3.0 * a.g.w[0] - chi);
+    const T s1 = (T)(1.0 / zeta), s2 = (T)(2.0 / zeta);
+    const T* vwin = a.Vp + ((size_t)qk * a.g.P2 + qj) * a.g.P1 + qi;
 
-        // t^0 = e_q (Eq. Rec:FD), t^{-1} = 0
-        for (int i = tid; i < G::ELEMS; i += G::NT) bufA[i] = 0;
-        if (DB) for (int i = tid; i < G::ELEMS; i += G::NT) bufB[i] = 0;
-        else for (int i = tid; i < G::NS; i += G::NT) bufB[i] = 0;
-        __syncthreads();
-        if (tid == 0) {
-            bufA[G::LEAD + M * G::PLANE + M * G::PX + M] = 1;
-            s_mom[0] = 1.0;
-        }
-        int ncand = 0;
-        if (has_nl) ncand = nl_setup<T, M>(a, sc, qi, qj, qk, red_i);
-        __syncthreads();
-
-        T* cur = bufA;
-        T* sec = bufB;
-        for (int i = 0; i < half; ++i) {
-            const T s = (i == 0) ? s1 : s2;
-            if (has_nl) {
-                nl_dots<T, M>(a, sc, cur, ncand);
-                __syncthreads();
-                nl_collect<T, M>(sc, ncand);
-                __syncthreads();
-                if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, s);
-                else nl_update<T, M, DB>(a, sc, sec, s);
-                __syncthreads();
-            }
-            T aa, ab, unused;
-            if (G::CY && (warp < FD_NO || warp >= G::S - FD_NO))   // warp-uniform
-                stencil_sweep<T, M, true, DB, true>(a, cur, sec, vwin, s, dshift, aa, ab, unused, &s_mom[i + 1]);
-            else
-                stencil_sweep<T, M, true, DB, false>(a, cur, sec, vwin, s, dshift, aa, ab, unused, &s_mom[i + 1]);
-            // t^{i+1}.t^{i+1} and t^{i+1}.t^i: column sums in T, warp trees, FP64 across warps
-            const int par = i & 1;
-            double w2 = warp_total(aa), w1 = warp_total(ab);
-            if (lane == 0) { red[par][0][warp] = w2; red[par][1][warp] = w1; }
-            __syncthreads();                       // also publishes the sweep and rho^{i+1}
-            if (tid == 0) {
-                double d2 = 0.0, d1 = 0.0;
-                for (int w = 0; w < G::NW; ++w) { d2 += red[par][0][w]; d1 += red[par][1][w]; }
-                s_d2[i + 1] = d2;                  // t^{i+1} . t^{i+1}
-                s_d1[i + 1] = d1;                  // t^{i+1} . t^i
-            }
-            if (DB) { T* t = cur; cur = sec; sec = t; }
-        }
-        __syncthreads();
-        double* out = a.moments + node * (long long)(a.npl + 1);
-        for (int j = tid; j <= a.npl; j += G::NT) {
-            double r;
-            if (j <= half) r = s_mom[j];
-            else if ((j & 1) == 0) r = 2.0 * s_d2[j / 2] - s_mom[0];        // rho^{2a} = 2 t^a.t^a - rho^0
-            else r = 2.0 * s_d1[(j + 1) / 2] - s_mom[1];                     // rho^{2a+1} = 2 t^{a+1}.t^a - rho^1
-            out[j] = r;
-            if (!(fabs(r) <= 1.0 + a.mom_tol)) atomicOr(a.err, ERR_BOUNDS);
-        }
-        __syncthreads();
+    // t^0 = e_q (Eq. Rec:FD), t^{-1} = 0
+    for (int i = tid; i < G::ELEMS; i += G::NT) bufA[i] = 0;
+    if (DB) for (int i = tid; i < G::ELEMS; i += G::NT) bufB[i] = 0;
+    else for (int i = tid; i < G::NS; i += G::NT) bufB[i] = 0;
+    __syncthreads();
+    if (tid == 0) {
+        bufA[G::LEAD + M * G::PLANE + M * G::PX + M] = 1;
+        s_mom[0] = 1.0;
     }
+    int ncand = 0;
+    if (has_nl) ncand = nl_setup<T, M>(a, sc, qi, qj, qk, red_i);
+    __syncthreads();
+
+    T* cur = bufA;
+    T* sec = bufB;
+    for (int i = 0; i < half; ++i) {
+        const T s = (i == 0) ? s1 : s2;
+        if (has_nl) {
+            nl_dots<T, M>(a, sc, cur, ncand);
+            __syncthreads();
+            nl_collect<T, M>(sc, ncand);
+            __syncthreads();
+            if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, s);
+            else nl_update<T, M, DB>(a, sc, sec, s);
+            __syncthreads();
+        }
+        T aa, ab, unused;
+        if (G::CY && (warp < FD_NO || warp >= G::S - FD_NO))   // warp-uniform
+            stencil_sweep<T, M, true, DB, true>(a, cur, sec, vwin, s, dshift, aa, ab, unused, &s_mom[i + 1]);
+        else
+            stencil_sweep<T, M, true, DB, false>(a, cur, sec, vwin, s, dshift, aa, ab, unused, &s_mom[i + 1]);
+        // t^{i+1}.t^{i+1} and t^{i+1}.t^i: column sums in T, warp trees, FP64 across warps
+        const int par = i & 1;
+        double w2 = warp_total(aa), w1 = warp_total(ab);
+        if (lane == 0) { red[par][0][warp] = w2; red[par][1][warp] = w1; }
+        __syncthreads();                       // also publishes the sweep and rho^{i+1}
+        if (tid == 0) {
+            double d2 = 0.0, d1 = 0.0;
+            for (int w = 0; w < G::NW; ++w) { d2 += red[par][0][w]; d1 += red[par][1][w]; }
+            s_d2[i + 1] = d2;                  // t^{i+1} . t^{i+1}
+            s_d1[i + 1] = d1;                  // t^{i+1} . t^i
+        }
+        if (DB) { T* t = cur; cur = sec; sec = t; }
+    }
+    __syncthreads();
+    double* out = a.moments + node * (long long)(a.npl + 1);
+    for (int j = tid; j <= a.npl; j += G::NT) {
+        double r;
+        if (j <= half) r = s_mom[j];
+        else if ((j & 1) == 0) r = 2.0 * s_d2[j / 2] - s_mom[0];        // rho^{2a} = 2 t^a.t^a - rho^0
+        else r = 2.0 * s_d1[(j + 1) / 2] - s_mom[1];                     // rho^{2a+1} = 2 t^{a+1}.t^a - rho^1
+        out[j] = r;
+        if (!(fabs(r) <= 1.0 + a.mom_tol)) atomicOr(a.err, ERR_BOUNDS);
+    }
+    __syncthreads();
+}
+
+template <typename T, int M, bool DB>
+__global__ void __launch_bounds__(Geo<M>::NT, (region_min_blocks<T, M>()))
+moments_kernel(RegionArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (long long node = blockIdx.x; node < a.g.Nd; node += gridDim.x) moments_node<T, M, DB>(a, smem_raw, node);
 }
 
 // ------------------------------------------------------------------------
@@ -998,13 +1002,11 @@ moments_kernel(RegionArgs<T> a)
 // (alpha, beta, breakdown test) runs on thread 0 in FP64 and is broadcast.
 // ------------------------------------------------------------------------
 template <typename T, int M, bool DB>
-__global__ void __launch_bounds__(Geo<M>::NT, (region_min_blocks<T, M>()))
-lanczos_kernel(RegionArgs<T> a)
+__device__ void lanczos_node(const RegionArgs<T>& a, unsigned char* smem_raw, long long node)
 {
     using G = Geo<M>;
     static_assert(!G::CY || DB, "compact regions must keep both vectors in shared memory");
     using SV = Sec<M, DB>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
     __shared__ double red_a[32], red_b[32], red_c[32];  // v.w, w.w and v.v partials
     __shared__ int red_i[33];
@@ -1022,129 +1024,134 @@ lanczos_kernel(RegionArgs<T> a)
     const T dshift = (T)(-3.0 * a.g.w[0]);
     const T v0 = (T)(1.0 / sqrt((double)G::NS));
 
-    for (long long node = blockIdx.x; node < a.g.Nd; node += gridDim.x) {
-        const int qi = (int)(node % a.g.n1);
-        const int qj = (int)((node / a.g.n1) % a.g.n2);
-        const int qk = (int)(node / ((long long)a.g.n1 * a.g.n2));
-        const T* vwin = a.Vp + ((size_t)qk * a.g.P2 + qj) * a.g.P1 + qi;
-        for (int i = tid; i < G::ELEMS; i += G::NT) sm[i] = 0;
-        if (DB) for (int i = tid; i < G::ELEMS; i += G::NT) sec[i] = 0;
-        else for (int i = tid; i < G::NS; i += G::NT) sec[i] = 0;
-        __syncthreads();
-        T* col = sm + G::LEAD + y * G::PX + x;
-        T* bcol = SV::col(sec, x, y);
-        if (active)
-            for (int z = 0; z < G::S; ++z) col[z * G::PLANE] = v0;
-        int ncand = 0;
-        if (has_nl) ncand = nl_setup<T, M>(a, sc, qi, qj, qk, red_i);
-        __syncthreads();
+    const int qi = (int)(node % a.g.n1);
+    const int qj = (int)((node / a.g.n1) % a.g.n2);
+    const int qk = (int)(node / ((long long)a.g.n1 * a.g.n2));
+    const T* vwin = a.Vp + ((size_t)qk * a.g.P2 + qj) * a.g.P1 + qi;
+    for (int i = tid; i < G::ELEMS; i += G::NT) sm[i] = 0;
+    if (DB) for (int i = tid; i < G::ELEMS; i += G::NT) sec[i] = 0;
+    else for (int i = tid; i < G::NS; i += G::NT) sec[i] = 0;
+    __syncthreads();
+    T* col = sm + G::LEAD + y * G::PX + x;
+    T* bcol = SV::col(sec, x, y);
+    if (active)
+        for (int z = 0; z < G::S; ++z) col[z * G::PLANE] = v0;
+    int ncand = 0;
+    if (has_nl) ncand = nl_setup<T, M>(a, sc, qi, qj, qk, red_i);
+    __syncthreads();
 
-        double* alpha = a.alpha + node * (long long)a.nl_cap;
-        double* beta = a.beta + node * (long long)a.nl_cap;
-        double bprev = 0.0, scale = 0.0;           // thread 0 only
-        for (int it = 0; it < a.n_lanczos; ++it) {
-            // w = H v - beta_prev v_old  (sec holds beta_prev v_old, then w)
-            if (has_nl) {
-                nl_dots<T, M>(a, sc, sm, ncand);
-                __syncthreads();
-                nl_collect<T, M>(sc, ncand);
-                __syncthreads();
-                if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, T(1));
-                else nl_update<T, M, DB>(a, sc, sec, T(1));
-                __syncthreads();
+    double* alpha = a.alpha + node * (long long)a.nl_cap;
+    double* beta = a.beta + node * (long long)a.nl_cap;
+    double bprev = 0.0, scale = 0.0;           // thread 0 only
+    for (int it = 0; it < a.n_lanczos; ++it) {
+        // w = H v - beta_prev v_old  (sec holds beta_prev v_old, then w)
+        if (has_nl) {
+            nl_dots<T, M>(a, sc, sm, ncand);
+            __syncthreads();
+            nl_collect<T, M>(sc, ncand);
+            __syncthreads();
+            if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, T(1));
+            else nl_update<T, M, DB>(a, sc, sec, T(1));
+            __syncthreads();
+        }
+        T ww, vw, vv;
+        if (G::CY && (warp < FD_NO || warp >= G::S - FD_NO))   // warp-uniform
+            stencil_sweep<T, M, false, DB, true>(a, sm, sec, vwin, T(1), dshift, ww, vw, vv, &s_dummy);
+        else
+            stencil_sweep<T, M, false, DB, false>(a, sm, sec, vwin, T(1), dshift, ww, vw, vv, &s_dummy);
+        // alpha = v.w and beta^2 = |w - alpha v|^2 = w.w - 2 alpha v.w + alpha^2 v.v from the
+        // sweep's sums, which saves a pass over w; where that difference cancels (beta below a
+        // tenth of |w|: near breakdown, e.g. tiny regions) beta is taken from w - alpha v itself
+        const double wa = warp_total(vw), wb = warp_total(ww), wc = warp_total(vv);
+        if (lane == 0) {
+            red_a[warp] = wa;
+            red_b[warp] = wb;
+            red_c[warp] = wc;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double al = 0.0, w2 = 0.0, v2 = 0.0;
+            for (int w = 0; w < G::NW; ++w) {
+                al += red_a[w];
+                w2 += red_b[w];
+                v2 += red_c[w];
             }
-            T ww, vw, vv;
-            if (G::CY && (warp < FD_NO || warp >= G::S - FD_NO))   // warp-uniform
-                stencil_sweep<T, M, false, DB, true>(a, sm, sec, vwin, T(1), dshift, ww, vw, vv, &s_dummy);
-            else
-                stencil_sweep<T, M, false, DB, false>(a, sm, sec, vwin, T(1), dshift, ww, vw, vv, &s_dummy);
-            // alpha = v.w and beta^2 = |w - alpha v|^2 = w.w - 2 alpha v.w + alpha^2 v.v from the
-            // sweep's sums, which saves a pass over w; where that difference cancels (beta below a
-            // tenth of |w|: near breakdown, e.g. tiny regions) beta is taken from w - alpha v itself
-            const double wa = warp_total(vw), wb = warp_total(ww), wc = warp_total(vv);
-            if (lane == 0) {
-                red_a[warp] = wa;
-                red_b[warp] = wb;
-                red_c[warp] = wc;
+            alpha[it] = al;
+            if (fabs(al) + bprev > scale) scale = fabs(al) + bprev;
+            const double b2 = w2 - 2.0 * al * al + al * al * v2;
+            s_alpha = (T)al;
+            s_explicit = !(b2 > 0.01 * w2);
+            if (!s_explicit) {
+                const double b = sqrt(b2);
+                const int stop = (it == a.n_lanczos - 1) || (b <= 1e-10 * scale);
+                if (!stop) beta[it] = b;
+                else a.klen[node] = it + 1;
+                s_stop = stop;
+                s_inv = (T)(1.0 / b);
+                s_bprev = (T)b;
+                bprev = b;
             }
+        }
+        __syncthreads();
+        const T alT = s_alpha;
+        if (s_explicit) {                              // block-uniform
+            // w -= alpha v ; beta = |w|
+            T acc = 0;
+            if (active)
+                for (int z = 0; z < G::S; ++z) {
+                    T w = bcol[z * SV::ZS] - alT * col[z * G::PLANE];
+                    bcol[z * SV::ZS] = w;
+                    acc += w * w;
+                }
+            const double wt = warp_total(acc);
+            if (lane == 0) red_b[warp] = wt;
             __syncthreads();
             if (tid == 0) {
-                double al = 0.0, w2 = 0.0, v2 = 0.0;
-                for (int w = 0; w < G::NW; ++w) {
-                    al += red_a[w];
-                    w2 += red_b[w];
-                    v2 += red_c[w];
-                }
-                alpha[it] = al;
-                if (fabs(al) + bprev > scale) scale = fabs(al) + bprev;
-                const double b2 = w2 - 2.0 * al * al + al * al * v2;
-                s_alpha = (T)al;
-                s_explicit = !(b2 > 0.01 * w2);
-                if (!s_explicit) {
-                    const double b = sqrt(b2);
-                    const int stop = (it == a.n_lanczos - 1) || (b <= 1e-10 * scale);
-                    if (!stop) beta[it] = b;
-                    else a.klen[node] = it + 1;
-                    s_stop = stop;
-                    s_inv = (T)(1.0 / b);
-                    s_bprev = (T)b;
-                    bprev = b;
-                }
+                double b2 = 0.0;
+                for (int w = 0; w < G::NW; ++w) b2 += red_b[w];
+                const double b = sqrt(b2);
+                const int stop = (it == a.n_lanczos - 1) || (b <= 1e-10 * scale);
+                if (!stop) beta[it] = b;
+                else a.klen[node] = it + 1;
+                s_stop = stop;
+                s_inv = (T)(1.0 / b);
+                s_bprev = (T)b;
+                bprev = b;
             }
             __syncthreads();
-            const T alT = s_alpha;
-            if (s_explicit) {                              // block-uniform
-                // w -= alpha v ; beta = |w|
-                T acc = 0;
-                if (active)
-                    for (int z = 0; z < G::S; ++z) {
-                        T w = bcol[z * SV::ZS] - alT * col[z * G::PLANE];
-                        bcol[z * SV::ZS] = w;
-                        acc += w * w;
-                    }
-                const double wt = warp_total(acc);
-                if (lane == 0) red_b[warp] = wt;
-                __syncthreads();
-                if (tid == 0) {
-                    double b2 = 0.0;
-                    for (int w = 0; w < G::NW; ++w) b2 += red_b[w];
-                    const double b = sqrt(b2);
-                    const int stop = (it == a.n_lanczos - 1) || (b <= 1e-10 * scale);
-                    if (!stop) beta[it] = b;
-                    else a.klen[node] = it + 1;
-                    s_stop = stop;
-                    s_inv = (T)(1.0 / b);
-                    s_bprev = (T)b;
-                    bprev = b;
+            if (s_stop) break;
+            // sec <- beta v (the next step's beta_prev v_old), v <- w / beta
+            const T inv = s_inv, bT = s_bprev;
+            if (active)
+                for (int z = 0; z < G::S; ++z) {
+                    T w = bcol[z * SV::ZS];
+                    T v = col[z * G::PLANE];
+                    bcol[z * SV::ZS] = bT * v;
+                    col[z * G::PLANE] = w * inv;
                 }
-                __syncthreads();
-                if (s_stop) break;
-                // sec <- beta v (the next step's beta_prev v_old), v <- w / beta
-                const T inv = s_inv, bT = s_bprev;
-                if (active)
-                    for (int z = 0; z < G::S; ++z) {
-                        T w = bcol[z * SV::ZS];
-                        T v = col[z * G::PLANE];
-                        bcol[z * SV::ZS] = bT * v;
-                        col[z * G::PLANE] = w * inv;
-                    }
-            } else {
-                if (s_stop) break;
-                // sec <- beta v, v <- (w - alpha v) / beta
-                const T inv = s_inv, bT = s_bprev;
-                if (active)
-                    for (int z = 0; z < G::S; ++z) {
-                        T w = bcol[z * SV::ZS];
-                        T v = col[z * G::PLANE];
-                        bcol[z * SV::ZS] = bT * v;
-                        col[z * G::PLANE] = (w - alT * v) * inv;
-                    }
-            }
-            __syncthreads();
+        } else {
+            if (s_stop) break;
+            // sec <- beta v, v <- (w - alpha v) / beta
+            const T inv = s_inv, bT = s_bprev;
+            if (active)
+                for (int z = 0; z < G::S; ++z) {
+                    T w = bcol[z * SV::ZS];
+                    T v = col[z * G::PLANE];
+                    bcol[z * SV::ZS] = bT * v;
+                    col[z * G::PLANE] = (w - alT * v) * inv;
+                }
         }
         __syncthreads();
     }
+    __syncthreads();
 }
 
+template <typename T, int M, bool DB>
+__global__ void __launch_bounds__(Geo<M>::NT, (region_min_blocks<T, M>()))
+lanczos_kernel(RegionArgs<T> a)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    for (long long node = blockIdx.x; node < a.g.Nd; node += gridDim.x) lanczos_node<T, M, DB>(a, smem_raw, node);
+}
 
 }  // namespace sq

@@ -24,7 +24,7 @@ SQ_FP64, SQ_FP32 = 0, 1
 EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments", "sq_fermi_level",
            "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
-           "sq_batch_destroy", "sq_poisson", "sq_widen_bounds", "sq_effective_potential", "sq_mixer_create",
+           "sq_batch_set_plan", "sq_batch_plan", "sq_batch_set_wait", "sq_batch_destroy", "sq_poisson", "sq_widen_bounds", "sq_effective_potential", "sq_mixer_create",
            "sq_mixer_step",
            "sq_mixer_set_period", "sq_mixer_history", "sq_mixer_export", "sq_mixer_import", "sq_mixer_reset", "sq_mixer_destroy",
            "sq_nl_forces", "sq_nl_forces_nodes", "sq_kerker", "sq_cnn_param_count", "sq_cnn_create",
@@ -77,6 +77,9 @@ def load(path: str = LIB_PATH):
         lib.sq_batch_run.argtypes = [vp, pp, pp, pp, pp, pp, dp, dp, ip, C.c_double]
         lib.sq_batch_results.argtypes = [vp, dp, dp, dp, dp]
         lib.sq_batch_blocks.argtypes = [vp, C.POINTER(ip)]
+        lib.sq_batch_set_plan.argtypes = [vp, ip, ip]
+        lib.sq_batch_plan.argtypes = [vp, C.POINTER(ip), C.POINTER(ip)]
+        lib.sq_batch_set_wait.argtypes = [vp, C.c_longlong, ip]
         lib.sq_batch_destroy.argtypes = [vp]
         lib.sq_batch_destroy.restype = None
         lib.sq_poisson.argtypes = [vp, vp, vp, C.c_double, ip, C.POINTER(ip), dp]
@@ -264,6 +267,24 @@ def sq_batch_blocks(batch, n):
     out = (C.c_int * n)()
     _check(load().sq_batch_blocks(C.c_void_p(batch), out), "sq_batch_blocks")
     return list(out)
+
+
+SQ_BATCH_AUTO, SQ_BATCH_STREAMS, SQ_BATCH_STREAMS_SHARE, SQ_BATCH_QUEUE = -1, 0, 1, 2
+
+
+def sq_batch_set_plan(batch, plan, nodes_per_item=1):
+    _check(load().sq_batch_set_plan(C.c_void_p(batch), int(plan), int(nodes_per_item)), "sq_batch_set_plan")
+
+
+def sq_batch_plan(batch):
+    """(plan, nodes_per_item) in use after the first run."""
+    p, k = C.c_int(0), C.c_int(0)
+    _check(load().sq_batch_plan(C.c_void_p(batch), C.byref(p), C.byref(k)), "sq_batch_plan")
+    return p.value, k.value
+
+
+def sq_batch_set_wait(batch, budget_cycles, wait_on_unset=0):
+    _check(load().sq_batch_set_wait(C.c_void_p(batch), int(budget_cycles), int(wait_on_unset)), "sq_batch_set_wait")
 
 
 def sq_batch_destroy(batch):

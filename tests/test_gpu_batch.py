@@ -1,10 +1,15 @@
 """Batched launch (sq_batch_*): the whole step of several uneven systems as
-one CUDA graph must give what the single-system calls give for each system
--- bit for bit in FP64 (every sum there has a fixed order and a node's result
-does not depend on the grid it runs in), and to FP32 rounding in FP32 (the
-projector update adds with shared-memory atomics).  The single-system calls
-are themselves pinned to the oracle by test_gpu_parity.py; one system here
-is also checked against the oracle on sampled nodes."""
+one CUDA graph must give what the single-system calls give for each system,
+in every launch plan (per-system streams, or persistent queue kernels per
+group of systems with one region size) -- bit for bit in FP64 (every sum
+there has a fixed order and a node's result does not depend on the CTA or
+grid it runs in), and to FP32 rounding in FP32 (the projector update adds
+with shared-memory atomics).  The single-system calls are themselves pinned
+to the oracle by test_gpu_parity.py; here one system of an FP64 batch and
+every system of the 16-system FP32 benchmark batch are also checked against
+the oracle on sampled nodes.  The queue plan's bounded waits are made to run
+out (a count that nothing completes) and must end the run with SQ_ETIMEOUT,
+leaving the batch usable."""
 import numpy as np
 import pytest
 
@@ -47,8 +52,12 @@ def _snapshot(solver, scal):
                 chi=solver.chi.cpu().numpy().copy(), **scal)
 
 
+PLANS = {"streams": (sq.SQ_BATCH_STREAMS, 1), "queue1": (sq.SQ_BATCH_QUEUE, 1), "queue5": (sq.SQ_BATCH_QUEUE, 5)}
+
+
+@pytest.mark.parametrize("plan", list(PLANS))
 @pytest.mark.parametrize("precision", [SQ_FP64, SQ_FP32])
-def test_batch_matches_single_system_calls(systems, precision):
+def test_batch_matches_single_system_calls(systems, precision, plan):
     Vs = [_dev(s.V) for s in systems]
     single = []
     for s, V in zip(systems, Vs):
@@ -59,6 +68,7 @@ def test_batch_matches_single_system_calls(systems, precision):
         solver.close()
     solvers = [SQSolver.from_workload(s.wl, s.positions, precision=precision, device=DEV) for s in systems]
     batch = SQBatch(solvers)
+    batch.set_plan(*PLANS[plan])
     args = ([s.wl.n_electrons for s in systems], [s.wl.kT for s in systems])
     runs = []
     for _ in range(2):                      # the second run replays the instantiated graph
@@ -67,6 +77,8 @@ def test_batch_matches_single_system_calls(systems, precision):
         runs.append([_snapshot(sv, r) for sv, r in zip(solvers, res)])
     blocks = batch.blocks()
     assert len(blocks) == len(systems) and all(b >= 0 for b in blocks)
+    kind, npi = batch.plan()
+    assert kind == PLANS[plan][0] and npi == (PLANS[plan][1] if kind == sq.SQ_BATCH_QUEUE else 0)
     for one, b1, b2 in zip(single, runs[0], runs[1]):
         if precision == SQ_FP64:
             for k in ("moments", "rho", "chi"):
@@ -121,6 +133,90 @@ def test_batch_rejects_bad_arguments(systems):
     with pytest.raises(SQError) as e:              # the C entry point itself, a NULL batch
         sq._check(sq.load().sq_batch_run(None, None, None, None, None, None, None, None, 40, 0.01), "sq_batch_run")
     assert e.value.code == sq.SQ_EINVAL
+    batch.close()
+    for x in solvers:
+        x.close()
+
+
+def test_batch_autotuner_picks_a_plan(systems):
+    solvers = [SQSolver.from_workload(s.wl, s.positions, precision=SQ_FP32, device=DEV) for s in systems]
+    batch = SQBatch(solvers)
+    batch.run([_dev(s.V) for s in systems], [s.wl.n_electrons for s in systems], [s.wl.kT for s in systems])
+    res = batch.results()
+    kind, npi = batch.plan()
+    assert kind in (sq.SQ_BATCH_STREAMS, sq.SQ_BATCH_STREAMS_SHARE, sq.SQ_BATCH_QUEUE)
+    assert (npi in (1, 4)) if kind == sq.SQ_BATCH_QUEUE else npi == 0
+    for s, r in zip(systems, res):
+        assert abs(r["n_elec"] - s.wl.n_electrons) < 1e-8 * s.wl.n_electrons
+    batch.close()
+    for x in solvers:
+        x.close()
+
+
+def test_queue_wait_runs_out_then_batch_recovers(systems):
+    """Every Lanczos item waits for one potential slab more than exist: each
+    wait ends after its budget (2e6 SM cycles, ~1 ms) and the run reports
+    SQ_ETIMEOUT; with normal waits the same batch then gives the single-system
+    results again."""
+    sub = systems[:3]
+    Vs = [_dev(s.V) for s in sub]
+    args = ([s.wl.n_electrons for s in sub], [s.wl.kT for s in sub])
+    solvers = [SQSolver.from_workload(s.wl, s.positions, precision=SQ_FP64, device=DEV) for s in sub]
+    batch = SQBatch(solvers)
+    batch.set_plan(sq.SQ_BATCH_QUEUE, 64)
+    batch.set_wait(2_000_000, wait_on_unset=True)
+    batch.run(Vs, *args)
+    with pytest.raises(SQError) as e:
+        batch.results()
+    assert e.value.code == sq.SQ_ETIMEOUT
+    batch.set_wait(2_000_000_000, wait_on_unset=False)
+    batch.run(Vs, *args)
+    res = batch.results()
+    for s, sv, V, r in zip(sub, solvers, Vs, res):
+        one = SQSolver.from_workload(s.wl, s.positions, precision=SQ_FP64, device=DEV)
+        out = one.solve(V, s.wl.n_electrons, s.wl.kT, s.wl.n_lanczos, s.wl.margin)
+        assert np.array_equal(sv.rho.cpu().numpy(), one.rho.cpu().numpy())
+        assert r["mu"] == out["mu"]
+        one.close()
+    with pytest.raises(SQError) as e:
+        batch.set_wait(0)
+    assert e.value.code == sq.SQ_EINVAL
+    with pytest.raises(SQError) as e:
+        batch.set_plan(sq.SQ_BATCH_QUEUE, 0)
+    assert e.value.code == sq.SQ_EINVAL
+    batch.close()
+    for x in solvers:
+        x.close()
+
+
+def test_batch16_fp32_every_system_against_oracle():
+    """The 16 systems of the batch benchmark (regions 15^3 to 31^3, n_pl 24
+    to 64), FP32, queue plan: on 3 seeded nodes of every system the bounds
+    and moments against the oracle's, and the density against the oracle's
+    density step on its own bounds and moments at the GPU's Fermi level.
+    Tolerances of the FP32 context: bounds 2e-4 relative, moments 2e-5,
+    density 3e-5 of the largest sampled value (the max-norm bound of FP32
+    densities)."""
+    wls = synth.batch_workloads()
+    systems = [synth.make_system(w) for w in wls]
+    solvers = [SQSolver.from_workload(s.wl, s.positions, precision=SQ_FP32, device=DEV) for s in systems]
+    batch = SQBatch(solvers)
+    batch.set_plan(sq.SQ_BATCH_QUEUE, 1)
+    margin, n_lz = wls[0].margin, wls[0].n_lanczos
+    batch.run([_dev(s.V) for s in systems], [w.n_electrons for w in wls], [w.kT for w in wls], n_lz, margin)
+    res = batch.results()
+    for i, (s, sv, r) in enumerate(zip(systems, solvers, res)):
+        nodes = synth.sample_nodes(s.wl.n_nodes, 3, seed=100 + i)
+        osys = oracle.OracleSystem.from_synth(s)
+        ochi, ozeta = osys.bounds(nodes, n_lz, margin)
+        np.testing.assert_allclose(sv.chi.cpu().numpy()[nodes], ochi, rtol=2e-4, err_msg=f"system {i}")
+        np.testing.assert_allclose(sv.zeta.cpu().numpy()[nodes], ozeta, rtol=2e-4, err_msg=f"system {i}")
+        omom = osys.moments(nodes, ochi, ozeta, s.wl.npl)
+        np.testing.assert_allclose(sv.moments.cpu().numpy()[nodes], omom, rtol=0, atol=2e-5, err_msg=f"system {i}")
+        orho, *_ = oracle.density_energy(oracle.cc_weights(omom), ochi, ozeta, r["mu"], s.wl.kT, s.wl.h)
+        got = sv.rho.cpu().numpy()[nodes]
+        assert np.abs(got - orho).max() < 3e-5 * np.abs(orho).max(), f"system {i}"
+        assert abs(r["n_elec"] - s.wl.n_electrons) < 1e-8 * s.wl.n_electrons
     batch.close()
     for x in solvers:
         x.close()

@@ -13,7 +13,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
-from paper_1708_07913_gb300 import SQ_FP64, SQSCF, SQSolver, build, sq  # noqa: E402
+from paper_1708_07913_gb300 import SQ_FP32, SQ_FP64, SQSCF, SQSolver, build, sq  # noqa: E402
 
 build()
 DEV = "cuda:0"
@@ -145,6 +145,36 @@ def test_widen_bounds_and_scf_that_reuses_them():
     print(f"SCF to 1e-8: plain {plain['iterations']} iterations ({plain['lanczos_runs']} Lanczos runs), "
           f"reusing bounds {reuse['iterations']} ({reuse['lanczos_runs']} Lanczos runs)")
     solver.close()
+
+
+def test_fp32_scf_refined_in_fp64_reaches_the_fp64_fixed_point():
+    """FP32 iterations until the residual is 1e-5, then an FP64 context of
+    the same grid and atoms takes over with the mixing history: the loop
+    converges to 1e-10, far below what FP32 rounding allows, and its density
+    is the FP64 SCF's fixed point (both end on FP64 solves with the same
+    enclosing-bound policy, up to the residual left)."""
+    wl = synth.custom_workload("scf8f", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1743)
+    s = synth.make_system(wl)
+    V_loc = _dev(s.V)
+    coarse = SQSolver.from_workload(wl, s.positions, precision=SQ_FP32, device=DEV)
+    fine = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    mixed = SQSCF(coarse, V_loc, wl.n_electrons, wl.kT, reuse_bounds=0.05, refine=(fine, 1e-5))
+    out = mixed.run(tol=1e-10, max_iter=80)
+    assert out["converged"] and out["refined_at"] is not None
+    assert out["residuals"][out["refined_at"] - 1] <= 1e-5 < out["residuals"][out["refined_at"] - 2]
+    rho_mixed = out["rho"].cpu().numpy().copy()
+    ref = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    plain = SQSCF(ref, V_loc, wl.n_electrons, wl.kT, reuse_bounds=0.05).run(tol=1e-10, max_iter=80)
+    assert plain["converged"]
+    # both fixed points use bounds widened from some earlier Lanczos run, so they agree to the effect of
+    # the bounds on the SQ approximation (cf. the bound-reuse test), not to rounding
+    np.testing.assert_allclose(rho_mixed, plain["rho"].cpu().numpy(), atol=2e-3 * np.abs(rho_mixed).max())
+    print(f"FP32 -> FP64 at iteration {out['refined_at']}: converged to 1e-10 in {out['iterations']} iterations "
+          f"(FP64 throughout: {plain['iterations']})")
+    mixed.close()
+    for x in (coarse, fine, ref):
+        x.close()
 
 
 def test_scf_checkpoint_and_resume(tmp_path):
