@@ -18,7 +18,7 @@
  *   - batched systems: sq_batch_* (one CUDA graph per step);
  *   - SCF loop: sq_poisson, sq_effective_potential, sq_kerker, sq_mixer_*;
  *   - learned SCF warm start: sq_cnn_*;
- *   - housekeeping: sq_set_stream, sq_sync, sq_launch_count, sq_destroy,
+ *   - housekeeping: sq_set_stream, sq_sync, sq_launch_count, sq_context_info, sq_destroy,
  *     sq_strerror.
  *
  * Conventions
@@ -477,6 +477,17 @@ int sq_sync(sq_ctx *ctx);
 
 /* Number of kernel launches this context has enqueued since creation. */
 long long sq_launch_count(const sq_ctx *ctx);
+
+/* Launch configuration the context chose (host only, no synchronisation).
+ * info_host: HOST array of n >= 4 ints receiving
+ *   [0] m, the region half-width in grid points (region side 2m+1);
+ *   [1] the largest number of projector candidates of any node;
+ *   [2] where the per-candidate projector tables live during the region
+ *       kernels: 0 global scratch, 1 all in shared memory, 2 the tables every
+ *       step reads in shared memory and the rest in global scratch;
+ *   [3] resident CTAs of the region kernels (per-CTA scratch slices).
+ * SQ_EINVAL for a NULL context or n < 4. */
+int sq_context_info(const sq_ctx *ctx, int *info_host, int n);
 
 /* Release all device memory of the context (NULL is a no-op). */
 void sq_destroy(sq_ctx *ctx);

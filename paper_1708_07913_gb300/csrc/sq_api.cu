@@ -251,7 +251,7 @@ RegionArgs<T> region_args(sq_ctx* c)
     a.nl.ivl = c->d_ivl;
     a.nl.lb = c->lb;
     a.nl.ccap = c->ccap;
-    a.nl.smem = c->nl_extra > 0;
+    a.nl.smem = c->nl_mode;
     a.nl.tile_start = c->d_tile_start;
     a.nl.tile_cand = c->d_tile_cand;
     for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
@@ -836,6 +836,7 @@ int batch_tune(sq_batch* b, const BatchArgs& A)
         float ms = 0.f;
         if (rc == SQ_OK) rc = batch_time(b, g, &ms);
         if (g) cudaGraphExecDestroy(g);
+        if (rc == SQ_EUNSUPPORTED && cands[k].kind == SQ_BATCH_QUEUE) continue;   // a group's kernel does not fit
         if (rc) return rc;
         if (k == 0 || ms < best) {
             best = ms;
@@ -939,12 +940,22 @@ int sq_setup_grid(sq_ctx** out, int n1, int n2, int n3, double h, int fd_half_or
     }
     if ((rcode = select_cluster_kernels(c))) { free_ctx(c); return rcode; }
     // projector tables of the candidates in shared memory when they fit next
-    // to the region vectors (both kernels must accept the size)
+    // to the region vectors (both kernels must accept the size): all of them,
+    // else the ones every step reads, else none.  SQ_NL_TABLES=global, hot or
+    // all in the environment caps the choice (for comparisons).
     int bm = 0, bl = 0;
     c->nl_extra = 0;
-    if (c->n_atoms > 0) {
-        c->nl_extra = nl_smem_bytes(c->ccap, 2 * m + 1, tsz);
-        if (region_blocks(c, 0, &bm) != SQ_OK || region_blocks(c, 1, &bl) != SQ_OK) c->nl_extra = 0;
+    c->nl_mode = NL_GLOBAL;
+    const char* env = getenv("SQ_NL_TABLES");
+    const int cap_mode = !env ? NL_ALL : strcmp(env, "global") == 0 ? NL_GLOBAL : strcmp(env, "hot") == 0 ? NL_HOT : NL_ALL;
+    for (int mode : {(int)NL_ALL, (int)NL_HOT}) {
+        if (c->n_atoms == 0 || cap_mode == NL_GLOBAL) break;
+        if (mode == NL_ALL && cap_mode == NL_HOT) continue;
+        c->nl_mode = mode;
+        c->nl_extra = nl_smem_bytes(mode, c->ccap, 2 * m + 1, c->lb, tsz);
+        if (region_blocks(c, 0, &bm) == SQ_OK && region_blocks(c, 1, &bl) == SQ_OK) break;
+        c->nl_mode = NL_GLOBAL;
+        c->nl_extra = 0;
     }
     if ((rcode = region_blocks(c, 0, &bm)) || (rcode = region_blocks(c, 1, &bl))) { free_ctx(c); return rcode; }
     c->grid_blocks = std::max(bm, bl);
@@ -1041,6 +1052,16 @@ int sq_sync(sq_ctx* c)
 }
 
 long long sq_launch_count(const sq_ctx* c) { return c ? c->launches : -1; }
+
+int sq_context_info(const sq_ctx* c, int* info, int n)
+{
+    if (!c || !info || n < 4) return SQ_EINVAL;
+    info[0] = c->g.m;
+    info[1] = c->ccap;
+    info[2] = c->nl_mode;
+    info[3] = c->grid_blocks;
+    return SQ_OK;
+}
 
 void sq_destroy(sq_ctx* c)
 {

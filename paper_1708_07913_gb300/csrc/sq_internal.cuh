@@ -27,7 +27,6 @@ constexpr int TILE = 8;              // node tile edge for projector candidate l
 constexpr int MAX_CAND = 512;        // projector candidates per node
 constexpr int ENTRIES_PER_ROW = 24;  // projector entries a region row may hold (FCC Al at h ~ 0.48: up to 14)
 constexpr int MAX_NPL = 512;
-constexpr int STAGE = 16;            // row entries staged per warp at a time in the projector update
 
 // Error bits latched on the device (combined into one sq_status on the host).
 constexpr unsigned ERR_BOUNDS = 1u;
@@ -53,7 +52,7 @@ struct NLParams {
     const int4* tile_cand;           // (atom, box start x, y, z) unwrapped
     int ntile[3];
     int ccap;                        // most candidates any node has (exact, from the set-up)
-    int smem;                        // 1: the per-candidate tables live in shared memory after the region vectors
+    int smem;                        // placement of the per-candidate tables: NL_GLOBAL, NL_ALL or NL_HOT (shared memory after the region vectors)
     T cs;                            // h^3 gamma_s A_s^2   (0 if no s channel)
     T cp;                            // h^3 gamma_p A_p^2   (0 if no p channel)
 };
@@ -61,9 +60,11 @@ struct NLParams {
 // Projector entry record: one (candidate, region row) pair whose clipped
 // support interval in x is non-empty, with the row's y/z Gaussian factors
 //   f0 = G_y G_z,  f1 = DG_y G_z,  f2 = G_y DG_z.
-// meta = key | xlo << 10 | xhi << 15, where key is the region row r = y + S z
-// in candidate order and the candidate index c in row order.  One 16-byte
-// load in FP32.
+// meta = key | xlo << 10 | xhi << 15 | (bx + 32) << 20, where key is the
+// region row r = y + S z in candidate order and the candidate index c in row
+// order, and bx (in [-31, 30]) the region column of the candidate's box start,
+// so that the passes over the entries need no candidate table for it.  One
+// 16-byte load in FP32.
 template <typename T>
 struct __align__(16) EntRec {
     uint32_t meta;
@@ -86,11 +87,10 @@ struct CtaScratch {
     int4* cand;                      // candidates (atom, bx, by, bz): box start relative to the region
     int* clen;                       // candidate box lengths len_x | len_y << 8 | len_z << 16
     T* P;                            // 4 per candidate: projector inner products (S, X, Y, Z)
-    T* TX;                           // S*2 per candidate: (G_x, DG_x) at region column x (0 outside its box)
+    T* TX;                           // 2*lb per candidate: (G_x, DG_x) at box column k (0 beyond the box)
     T* seg;                          // 4 per (candidate + warp): partial inner products of one warp
     EntRec<T>* cent;                 // candidate-ordered entries
     EntRec<T>* rec;                  // row-ordered entries, ENTRIES_PER_ROW per row
-    EntRec<T>* stage;                // STAGE per warp: (meta, b0, b1) of the entries of the row in hand
     int* cand_start;                 // ncand + 1
     int* chunk_first;                // ncand + 1
     uint8_t* row_n;                  // S^2: entries of each row
@@ -147,6 +147,7 @@ struct sq_ctx {
     int lb;
     int ccap;                        // most projector candidates of any node
     size_t nl_extra;                 // shared-memory bytes of the candidate tables (0: in global scratch)
+    int nl_mode;                     // their placement: NL_GLOBAL, NL_ALL or NL_HOT (sq_region.cuh)
     int* d_tile_start;
     int4* d_tile_cand;
     int ntile[3];

@@ -24,15 +24,15 @@ namespace sq {
 template <int M>
 struct Geo {
     static constexpr int S = 2 * M + 1;
-    // Compact form for 27^3 and 29^3 regions (m = 13, 14): rows of pitch S+4
-    // (4 zero columns) and planes of exactly S rows, so that two vectors fit a
-    // CTA's shared memory (two fully padded 29^3 vectors would not); the
-    // stencil then masks the x neighbours at distance 5 and 6 of the edge
-    // columns and the y neighbours that fall outside the region, instead of
-    // reading zero halos.  LEAD and the 6-element tail keep every x-neighbour
-    // address inside the buffer.
+    // Compact form for 27^3 and 29^3 regions (m = 13, 14): rows of pitch S+2
+    // (2 zero columns) and planes of exactly S rows, so that two vectors and
+    // the hot projector tables fit a CTA's shared memory (two fully padded
+    // 29^3 vectors would not fit at all); the stencil then masks the x
+    // neighbours at distance 3 to 6 of the edge columns and the y neighbours
+    // that fall outside the region, instead of reading zero halos.  LEAD and
+    // the 6-element tail keep every x-neighbour address inside the buffer.
     static constexpr bool CY = (M == 13 || M == 14);
-    static constexpr int PX = CY ? S + 4 : S + 6;
+    static constexpr int PX = CY ? S + 2 : S + 6;
     static constexpr int PY = CY ? S : S + 6;
     static constexpr int PLANE = PX * PY;
     static constexpr int LEAD = CY ? 6 : 6 * PX + 6;
@@ -88,7 +88,7 @@ __host__ __device__ constexpr size_t region_smem()
 
 // Per-CTA scratch carving (identical on host and device).
 struct ScratchLayout {
-    size_t buf, cand, clen, P, TX, seg, cent, rec, stage, cand_start, chunk_first, row_n, total;
+    size_t buf, cand, clen, P, TX, seg, cent, rec, cand_start, chunk_first, row_n, total;
 };
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
@@ -103,11 +103,10 @@ __host__ __device__ inline ScratchLayout scratch_layout(int m, size_t tsize)
     L.cand = off;        off = align256(off + (size_t)MAX_CAND * sizeof(int4));
     L.clen = off;        off = align256(off + (size_t)MAX_CAND * sizeof(int));
     L.P = off;           off = align256(off + (size_t)MAX_CAND * 4 * tsize);
-    L.TX = off;          off = align256(off + (size_t)MAX_CAND * S * 2 * tsize);
+    L.TX = off;          off = align256(off + (size_t)MAX_CAND * NL_BOX * 2 * tsize);
     L.seg = off;         off = align256(off + (size_t)(MAX_CAND + 32) * 4 * tsize);
     L.cent = off;        off = align256(off + cap * rec_size(tsize));
     L.rec = off;         off = align256(off + cap * rec_size(tsize));
-    L.stage = off;       off = align256(off + (size_t)32 * STAGE * rec_size(tsize));
     L.cand_start = off;  off = align256(off + (size_t)(MAX_CAND + 1) * sizeof(int));
     L.chunk_first = off; off = align256(off + (size_t)(MAX_CAND + 1) * sizeof(int));
     L.row_n = off;       off = align256(off + (size_t)S * S);
@@ -116,30 +115,36 @@ __host__ __device__ inline ScratchLayout scratch_layout(int m, size_t tsize)
 }
 
 // Shared-memory placement of the per-candidate tables for ccap candidates
-// (offsets from a 16-byte aligned base; total includes 16 bytes of slack for
-// aligning that base).
+// with x-tables of lb box columns (offsets from a 16-byte aligned base; total
+// includes 16 bytes of slack for aligning that base).  NL_ALL: every table;
+// NL_HOT: only those read every step (inner products, x-tables, chunk and
+// entry offsets), the rest staying in global scratch, for regions whose
+// vectors leave too little room for all of them.
+enum : int { NL_GLOBAL = 0, NL_ALL = 1, NL_HOT = 2 };
 struct NLSmem {
-    size_t cand, P, TX, seg, stage, clen, cand_start, chunk_first, row_n, total;
+    size_t cand, P, TX, seg, clen, cand_start, chunk_first, row_n, total;
 };
-__host__ __device__ inline NLSmem nl_smem_layout(int ccap, int S, size_t tsize)
+__host__ __device__ inline NLSmem nl_smem_layout(int mode, int ccap, int S, int lb, size_t tsize)
 {
     NLSmem L;
     size_t o = 0;
-    L.cand = o;        o = align16(o + (size_t)ccap * sizeof(int4));
     L.P = o;           o = align16(o + (size_t)ccap * 4 * tsize);
-    L.TX = o;          o = align16(o + (size_t)ccap * 2 * S * tsize);
-    L.seg = o;         o = align16(o + (size_t)(ccap + 32) * 4 * tsize);
-    L.stage = o;       o = align16(o + (size_t)S * STAGE * rec_size(tsize));
-    L.clen = o;        o = align16(o + (size_t)ccap * sizeof(int));
+    L.TX = o;          o = align16(o + (size_t)ccap * 2 * lb * tsize);
     L.cand_start = o;  o = align16(o + (size_t)(ccap + 1) * sizeof(int));
     L.chunk_first = o; o = align16(o + (size_t)(ccap + 1) * sizeof(int));
-    L.row_n = o;       o = align16(o + (size_t)S * S);
+    L.cand = L.seg = L.clen = L.row_n = 0;
+    if (mode == NL_ALL) {
+        L.cand = o;    o = align16(o + (size_t)ccap * sizeof(int4));
+        L.seg = o;     o = align16(o + (size_t)(ccap + 32) * 4 * tsize);
+        L.clen = o;    o = align16(o + (size_t)ccap * sizeof(int));
+        L.row_n = o;   o = align16(o + (size_t)S * S);
+    }
     L.total = o + 16;
     return L;
 }
-__host__ __device__ inline size_t nl_smem_bytes(int ccap, int S, size_t tsize)
+__host__ __device__ inline size_t nl_smem_bytes(int mode, int ccap, int S, int lb, size_t tsize)
 {
-    return nl_smem_layout(ccap, S, tsize).total;
+    return nl_smem_layout(mode, ccap, S, lb, tsize).total;
 }
 
 // Per-node moment scratch of the moments kernel in dynamic shared memory:
@@ -183,29 +188,29 @@ __device__ inline CtaScratch<T> cta_scratch(const RegionArgs<T>& a, int m)
     s.seg = reinterpret_cast<T*>(base + L.seg);
     s.cent = reinterpret_cast<EntRec<T>*>(base + L.cent);
     s.rec = reinterpret_cast<EntRec<T>*>(base + L.rec);
-    s.stage = reinterpret_cast<EntRec<T>*>(base + L.stage);
     s.cand_start = reinterpret_cast<int*>(base + L.cand_start);
     s.chunk_first = reinterpret_cast<int*>(base + L.chunk_first);
     s.row_n = reinterpret_cast<uint8_t*>(base + L.row_n);
     return s;
 }
 
-// Move the per-candidate tables into shared memory at p (at least
-// nl_smem_bytes(ccap, S, sizeof(T)) bytes available).
+// Move the per-candidate tables of placement `mode` (NL_ALL or NL_HOT) into
+// shared memory at p (at least nl_smem_bytes(mode, ...) bytes available).
 template <typename T>
-__device__ inline void nl_tables_in_smem(CtaScratch<T>& s, void* p_, int ccap, int S)
+__device__ inline void nl_tables_in_smem(CtaScratch<T>& s, void* p_, int mode, int ccap, int S, int lb)
 {
     char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p_) + 15) & ~uintptr_t(15));
-    const NLSmem L = nl_smem_layout(ccap, S, sizeof(T));
-    s.cand = reinterpret_cast<int4*>(p + L.cand);
+    const NLSmem L = nl_smem_layout(mode, ccap, S, lb, sizeof(T));
     s.P = reinterpret_cast<T*>(p + L.P);
     s.TX = reinterpret_cast<T*>(p + L.TX);
-    s.seg = reinterpret_cast<T*>(p + L.seg);
-    s.stage = reinterpret_cast<EntRec<T>*>(p + L.stage);
-    s.clen = reinterpret_cast<int*>(p + L.clen);
     s.cand_start = reinterpret_cast<int*>(p + L.cand_start);
     s.chunk_first = reinterpret_cast<int*>(p + L.chunk_first);
-    s.row_n = reinterpret_cast<uint8_t*>(p + L.row_n);
+    if (mode == NL_ALL) {
+        s.cand = reinterpret_cast<int4*>(p + L.cand);
+        s.seg = reinterpret_cast<T*>(p + L.seg);
+        s.clen = reinterpret_cast<int*>(p + L.clen);
+        s.row_n = reinterpret_cast<uint8_t*>(p + L.row_n);
+    }
 }
 
 template <typename T>
@@ -375,15 +380,15 @@ __device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi,
     if (ncand > lim) ncand = lim;
     for (int c = tid; c <= ncand; c += G::NT) sc.cand_start[c] = 0;     // entry counts first
     __syncthreads();
-    // (2) x-tables of the candidates in region columns
-    for (int i = tid; i < ncand * G::S; i += G::NT) {
-        int c = i / G::S, x = i % G::S;
-        int4 cr = sc.cand[c];
-        int ii = x - cr.y;
+    // (2) x-tables of the candidates by box column k (lb per candidate; zero
+    // beyond the box)
+    for (int i = tid; i < ncand * lb; i += G::NT) {
+        const int c = i / lb, k = i % lb;
         T g = 0, dg = 0;
-        if (ii >= 0 && ii < (sc.clen[c] & 255)) {
-            g = nl.G[(size_t)cr.x * 3 * lb + ii];
-            dg = nl.DG[(size_t)cr.x * 3 * lb + ii];
+        if (k < (sc.clen[c] & 255)) {
+            const int atom = sc.cand[c].x;
+            g = nl.G[(size_t)atom * 3 * lb + k];
+            dg = nl.DG[(size_t)atom * 3 * lb + k];
         }
         sc.TX[2 * i] = g;
         sc.TX[2 * i + 1] = dg;
@@ -406,8 +411,8 @@ __device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi,
                 const T* Gt = nl.G + (size_t)cr.x * 3 * lb;
                 const T* Dt = nl.DG + (size_t)cr.x * 3 * lb;
                 const T gy = Gt[lb + jj], dgy = Dt[lb + jj], gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
-                st_rec<T>(out + n, (uint32_t)c | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15), gy * gz, dgy * gz,
-                          gy * dgz);
+                st_rec<T>(out + n, (uint32_t)c | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15) |
+                                       ((uint32_t)(cr.y + 32) << 20), gy * gz, dgy * gz, gy * dgz);
             } else {
                 atomicOr(a.err, ERR_CAPACITY);
             }
@@ -467,8 +472,8 @@ __device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi,
                 if (ce < cend) {
                     const int row = (cr.z + jj) + G::S * (cr.w + kk);
                     const T gy = Gt[lb + jj], dgy = Dt[lb + jj], gz = Gt[2 * lb + kk], dgz = Dt[2 * lb + kk];
-                    st_rec<T>(sc.cent + ce, (uint32_t)row | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15), gy * gz,
-                              dgy * gz, gy * dgz);
+                    st_rec<T>(sc.cent + ce, (uint32_t)row | ((uint32_t)xlo << 10) | ((uint32_t)xhi << 15) |
+                                                ((uint32_t)(cr.y + 32) << 20), gy * gz, dgy * gz, gy * dgz);
                 }
             }
             cnt += __popc(bal);
@@ -513,7 +518,8 @@ __device__ void nl_dots(const RegionArgs<T>& a, const CtaScratch<T>& sc, const T
         if (sc.chunk_first[mid] <= j0) lo = mid;
         else hi = mid - 1;
     }
-    const bool unrolled = a.nl.lb <= LBMAX;
+    const int lb = a.nl.lb;
+    const bool unrolled = lb <= LBMAX;
     // records of chunks j+1 and j+2 are in flight while chunk j is reduced
     auto fetch = [&](int j, int c, EntRec<T>& r, bool& v) {
         const int e = sc.cand_start[c] + (j - sc.chunk_first[c]) * 32 + lane;
@@ -544,17 +550,16 @@ __device__ void nl_dots(const RegionArgs<T>& a, const CtaScratch<T>& sc, const T
         }
         if (val) {
             const int r = rc.meta & 1023u, xlo = (rc.meta >> 10) & 31u, xhi = (rc.meta >> 15) & 31u;
+            const int bx = (int)((rc.meta >> 20) & 63u) - 32;
             const int y = r % G::S, z = r / G::S;
             const T* row = cur + G::LEAD + z * G::PLANE + y * G::PX;
-            const P2* tx = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * G::S;
+            // slots k of the candidate's box, x = bx + k: every lane of the
+            // chunk reads the same (G, DG) pair, and rows of one plane sit in
+            // distinct banks
+            const P2* txp = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * lb;
+            const T* rowp = row + bx;
             T u = 0, u2 = 0;
             if (unrolled) {
-                // slots k of the candidate's box, x = bx + k: every lane of the
-                // chunk reads the same (G, DG) pair, and rows of one plane sit
-                // in distinct banks
-                const int bx = sc.cand[c].y;
-                const T* rowp = row + bx;
-                const P2* txp = tx + bx;
                 const uint32_t mask = ((2u << (xhi - bx)) - 1u) & ~((1u << (xlo - bx)) - 1u);
 #pragma unroll
                 for (int k = 0; k < LBMAX; ++k)
@@ -565,9 +570,9 @@ __device__ void nl_dots(const RegionArgs<T>& a, const CtaScratch<T>& sc, const T
                         u2 += g.y * tv;
                     }
             } else {
-                for (int x = xlo; x <= xhi; ++x) {
-                    const P2 g = tx[x];
-                    const T tv = row[x];
+                for (int k = xlo - bx; k <= xhi - bx; ++k) {
+                    const P2 g = txp[k];
+                    const T tv = rowp[k];
                     u += g.x * tv;
                     u2 += g.y * tv;
                 }
@@ -680,11 +685,12 @@ __device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* se
         if (k + 2 < n) r1 = ld_rec(rrow + k + 2);
         if (k >= n) continue;
         const int c = rc.meta & 1023u, xlo = (rc.meta >> 10) & 31u, xhi = (rc.meta >> 15) & 31u;
+        const int bx = (int)((rc.meta >> 20) & 63u) - 32;
         T pS, pX, pY, pZ;
         load_P<T>(sc.P, c, pS, pX, pY, pZ);
         const T b0 = cs * rc.f0 * pS + cp * (rc.f1 * pY + rc.f2 * pZ);
         const T b1 = cp * rc.f0 * pX;
-        const P2* tx = tx2 + (size_t)c * G::S + xlo;
+        const P2* tx = tx2 + (size_t)c * a.nl.lb + (xlo - bx);
         T* bp = brow + xlo;
         const int len = xhi - xlo;                    // slots 0..len
         bool done = false;
@@ -741,7 +747,8 @@ __device__ void nl_update_red(const RegionArgs<T>& a, const CtaScratch<T>& sc, T
         if (sc.chunk_first[mid] <= j0) lo = mid;
         else hi = mid - 1;
     }
-    const bool unrolled = a.nl.lb <= LBMAX;
+    const int lb = a.nl.lb;
+    const bool unrolled = lb <= LBMAX;
     const T cs = a.nl.cs * coef, cp = a.nl.cp * coef;
     auto fetch = [&](int j, int c, EntRec<T>& r, bool& v) {
         const int e = sc.cand_start[c] + (j - sc.chunk_first[c]) * 32 + lane;
@@ -771,31 +778,31 @@ __device__ void nl_update_red(const RegionArgs<T>& a, const CtaScratch<T>& sc, T
         }
         if (!val) continue;
         const int r = rc.meta & 1023u, xlo = (rc.meta >> 10) & 31u, xhi = (rc.meta >> 15) & 31u;
+        const int bx = (int)((rc.meta >> 20) & 63u) - 32;
         T pS, pX, pY, pZ;
         load_P<T>(sc.P, c, pS, pX, pY, pZ);
         const T b0 = cs * rc.f0 * pS + cp * (rc.f1 * pY + rc.f2 * pZ);
         const T b1 = cp * rc.f0 * pX;
-        T* row = Sec<M, DB>::row(sec, r % G::S, r / G::S);
-        const P2* tx = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * G::S;
+        T* rowp = Sec<M, DB>::row(sec, r % G::S, r / G::S) + bx;
+        const P2* txp = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * lb;
         if (unrolled) {
-            const int bx = sc.cand[c].y;
             const uint32_t mask = ((2u << (xhi - bx)) - 1u) & ~((1u << (xlo - bx)) - 1u);
 #pragma unroll
             for (int k = 0; k < LBMAX; ++k)
                 if (mask & (1u << k)) {
-                    const P2 g = tx[bx + k];
+                    const P2 g = txp[k];
                     const T d = -(g.x * b0 + g.y * b1);
                     if constexpr (DB) {
-                        const unsigned addr = (unsigned)__cvta_generic_to_shared(row + bx + k);
+                        const unsigned addr = (unsigned)__cvta_generic_to_shared(rowp + k);
                         asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(d) : "memory");
                     } else {
-                        atomicAdd(row + bx + k, d);
+                        atomicAdd(rowp + k, d);
                     }
                 }
         } else {
-            for (int x = xlo; x <= xhi; ++x) {
-                const P2 g = tx[x];
-                atomicAdd(row + x, -(g.x * b0 + g.y * b1));
+            for (int k = xlo - bx; k <= xhi - bx; ++k) {
+                const P2 g = txp[k];
+                atomicAdd(rowp + k, -(g.x * b0 + g.y * b1));
             }
         }
     }
@@ -851,8 +858,8 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
 #pragma unroll
             for (int d = 1; d <= FD_NO; ++d) {
                 T xp = p[d], xm = p[-d];
-                if constexpr (G::CY) {                 // beyond the 4 zero columns: the next/previous row
-                    if (d >= 5) {
+                if constexpr (G::CY) {                 // beyond the zero columns: the next/previous row
+                    if (d > G::PX - G::S) {
                         if (x + d >= G::S) xp = T(0);
                         if (x < d) xm = T(0);
                     }
@@ -915,7 +922,7 @@ __device__ void moments_node(const RegionArgs<T>& a, unsigned char* smem_raw, lo
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     CtaScratch<T> sc = cta_scratch(a, M);
-    if (a.nl.smem) nl_tables_in_smem(sc, s_d1 + (a.npl / 2 + 2), a.nl.ccap, G::S);
+    if (a.nl.smem) nl_tables_in_smem(sc, s_d1 + (a.npl / 2 + 2), a.nl.smem, a.nl.ccap, G::S, a.nl.lb);
     T* bufB = DB ? bufA + G::ELEMS : sc.buf;
     const int half = a.npl / 2;
     const bool has_nl = a.nl.n_atoms > 0;
@@ -1018,7 +1025,7 @@ __device__ void lanczos_node(const RegionArgs<T>& a, unsigned char* smem_raw, lo
     const int x = lane, y = warp;
     const bool active = x < G::S;
     CtaScratch<T> sc = cta_scratch(a, M);
-    if (a.nl.smem) nl_tables_in_smem(sc, smem_raw + region_smem<T, M>(), a.nl.ccap, G::S);
+    if (a.nl.smem) nl_tables_in_smem(sc, smem_raw + region_smem<T, M>(), a.nl.smem, a.nl.ccap, G::S, a.nl.lb);
     T* sec = DB ? sm + G::ELEMS : sc.buf;
     const bool has_nl = a.nl.n_atoms > 0;
     const T dshift = (T)(-3.0 * a.g.w[0]);

@@ -22,7 +22,7 @@ SQ_FP64, SQ_FP32 = 0, 1
 
 # Every entry point declared in include/sq.h.
 EXPORTS = ("sq_setup_grid", "sq_set_stream", "sq_spectral_bounds", "sq_moments", "sq_fermi_level",
-           "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_destroy",
+           "sq_density_energy", "sq_density_energy_noalloc", "sq_sync", "sq_launch_count", "sq_context_info", "sq_destroy",
            "sq_strerror", "sq_batch_create", "sq_batch_run", "sq_batch_results", "sq_batch_blocks",
            "sq_batch_set_plan", "sq_batch_plan", "sq_batch_set_wait", "sq_batch_destroy", "sq_poisson", "sq_widen_bounds", "sq_effective_potential", "sq_mixer_create",
            "sq_mixer_step",
@@ -68,6 +68,7 @@ def load(path: str = LIB_PATH):
         lib.sq_sync.argtypes = [vp]
         lib.sq_launch_count.argtypes = [vp]
         lib.sq_launch_count.restype = C.c_longlong
+        lib.sq_context_info.argtypes = [vp, C.POINTER(ip), ip]
         lib.sq_destroy.argtypes = [vp]
         lib.sq_destroy.restype = None
         lib.sq_strerror.argtypes = [ip]
@@ -222,6 +223,18 @@ def sq_sync(ctx):
 
 def sq_launch_count(ctx) -> int:
     return int(load().sq_launch_count(C.c_void_p(ctx)))
+
+
+NL_GLOBAL, NL_ALL, NL_HOT = 0, 1, 2
+
+
+def sq_context_info(ctx) -> dict:
+    """The launch configuration the context chose: region half-width m, the
+    most projector candidates of any node, the projector-table placement
+    (NL_GLOBAL / NL_ALL / NL_HOT) and the region kernels' resident CTAs."""
+    out = (C.c_int * 4)()
+    _check(load().sq_context_info(C.c_void_p(ctx), out, 4), "sq_context_info")
+    return dict(m=out[0], ccap=out[1], tables=out[2], blocks=out[3])
 
 
 def sq_destroy(ctx):

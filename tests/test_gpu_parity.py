@@ -268,6 +268,45 @@ def test_largest_regions_fp32_sampled(r_cut, count):
     assert e.value.code == sq.SQ_EUNSUPPORTED
 
 
+@pytest.mark.parametrize("r_cut,placements", [(7.0, ("hot", "global")), (6.0, ("all", "hot", "global"))])
+def test_projector_table_placements(r_cut, placements, monkeypatch):
+    """The per-candidate projector tables in shared memory (all of them, or
+    only those every step reads, with the rest in global scratch) or all in
+    global scratch (SQ_NL_TABLES caps the choice at context creation): one
+    FCC cell on a 16^3 grid with R_cut = 7 (m = 14, the compact 29^3 layout,
+    where only the hot tables fit) and R_cut = 6 (m = 12, 25^3).  Each
+    placement matches the oracle's bounds and moments on sampled nodes, and
+    the placements agree with each other to FP32 rounding."""
+    wl = synth.custom_workload("place", cells=1, n=16, r_cut=r_cut, npl=32, kT=0.1, sigma_disp=0.15,
+                               nonlocal_=True, seed=1745)
+    s = synth.make_system(wl)
+    nodes = synth.sample_nodes(wl.n_nodes, 4, seed=5)
+    osys = oracle.OracleSystem.from_synth(s)
+    ochi, ozeta = osys.bounds(nodes, wl.n_lanczos, wl.margin)
+    omom = osys.moments(nodes, ochi, ozeta, wl.npl)
+    V = _dev(s.V)
+    chi_in = torch.full((wl.n_nodes,), float(np.median(ochi)), dtype=torch.float64, device=DEV)
+    zeta_in = torch.full((wl.n_nodes,), float(np.max(ozeta)) * 1.05, dtype=torch.float64, device=DEV)
+    idx = torch.from_numpy(nodes).to(DEV)
+    chi_in[idx] = _dev(ochi)
+    zeta_in[idx] = _dev(ozeta)
+    code = {"global": sq.NL_GLOBAL, "all": sq.NL_ALL, "hot": sq.NL_HOT}
+    moms = {}
+    for p in placements:
+        monkeypatch.setenv("SQ_NL_TABLES", p)
+        solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP32, device=DEV)
+        info = sq.sq_context_info(solver.ctx)
+        assert info["m"] == wl.m and info["tables"] == code[p], info
+        chi, zeta = solver.bounds(V, wl.n_lanczos, wl.margin)
+        np.testing.assert_allclose(chi.cpu().numpy()[nodes], ochi, rtol=2e-4)
+        np.testing.assert_allclose(zeta.cpu().numpy()[nodes], ozeta, rtol=2e-4)
+        moms[p] = solver.compute_moments(V, chi_in, zeta_in).cpu().numpy()
+        np.testing.assert_allclose(moms[p][nodes], omom, rtol=0, atol=FP32_MOM)
+        solver.close()
+    for p in placements[1:]:
+        assert np.abs(moms[p] - moms[placements[0]]).max() < FP32_MOM
+
+
 def test_errors_are_reported_not_faulted():
     s = synth.make_system("al4_16")
     wl = s.wl
