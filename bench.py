@@ -30,6 +30,7 @@ from __future__ import annotations
 
 import argparse
 import collections
+import dataclasses
 import hashlib
 import json
 import math
@@ -59,7 +60,7 @@ SM_COUNT_GB300 = 152
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=2)
+    p.add_argument("--steps", type=int, default=1)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--precision", choices=["fp32", "fp64"], default="fp32")
     p.add_argument("--workload", default=WORKLOAD)
@@ -67,6 +68,11 @@ def parse():
     p.add_argument("--cpu-sample", type=int, default=0, help="oracle sample size (nodes); 0 = automatic")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-fp64-context", action="store_true", help="skip the FP64-vs-FP32 comparison on al108_48")
+    p.add_argument("--n-lanczos", type=int, default=0,
+                   help="override the workload's Lanczos step count (an ablation; 0: the workload's)")
+    p.add_argument("--margin", type=float, default=0.0,
+                   help="with --n-lanczos: the bounds' relative widening (0: the workload's)")
+    p.add_argument("--save-rho", default="", help="write the last step's density (float32 .npy) to this path")
     p.add_argument("--refine-at", default="none",
                    help="scf_*, warmstart_c4: residual at which an FP64 context takes over (none: FP32 throughout)")
     p.add_argument("--batch-plan", choices=["auto", "streams", "share", "queue"], default="auto",
@@ -337,6 +343,8 @@ def run_gb300(a):
     prec = SQ_FP32 if a.precision == "fp32" else SQ_FP64
     s = synth.make_system(a.workload)
     wl = s.wl
+    if a.n_lanczos > 0:                                    # ablation of the bounds' cost
+        wl = dataclasses.replace(wl, n_lanczos=a.n_lanczos, margin=a.margin if a.margin > 0 else wl.margin)
     solver = SQSolver.from_workload(wl, s.positions, precision=prec, device=str(dev))
     Vh = torch.from_numpy(s.V.ravel().copy()).pin_memory()
     V = Vh.to(dev)
@@ -392,6 +400,8 @@ def run_gb300(a):
         torch.cuda.synchronize()
         e2e_t.append(time.perf_counter() - t0)
     clk = clocks.stop()
+    if a.save_rho:
+        np.save(a.save_rho, rho_h.numpy().astype(np.float32))
 
     per = np.array([[e[i].elapsed_time(e[i + 1]) for i in range(4)] for e in timed])   # ms
     step_ms = per.sum(axis=1)
@@ -428,7 +438,8 @@ def run_gb300(a):
         "config": {"workload": workload_desc(a.workload, wl),
                    "precision": ("FP32 recurrence/Lanczos vectors, FP64 moments, weights, Fermi level, energies"
                                  if prec == SQ_FP32 else "FP64 throughout"),
-                   "n_lanczos": wl.n_lanczos, "l2": "flushed between timed steps (256 MB write)",
+                   "n_lanczos": wl.n_lanczos, "margin": wl.margin,
+                   "lanczos_override": a.n_lanczos > 0, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "breakdown_s": {"bounds": t_bounds, "moments": t_mom, "fermi": t_fermi, "density": t_dens},
         "moments_only_node_moments_per_s": wl.n_nodes * wl.npl * world / t_mom,
