@@ -750,12 +750,17 @@ def run_force(a):
                                f"a projector support",
                    "precision": ("FP32 recurrence, D and projector sums; FP64 coefficients and contraction"
                                  if prec == SQ_FP32 else "FP64 throughout"),
-                   "vector_storage": ("current vector in shared memory (SQ_FORCE_SMEM=1)"
-                                      if os.environ.get("SQ_FORCE_SMEM") == "1" else "global scratch"),
+                   "kernel": ("first form, current vector in shared memory (SQ_FORCE_KERNEL=legacy, SQ_FORCE_SMEM=1)"
+                              if os.environ.get("SQ_FORCE_KERNEL") == "legacy" and os.environ.get("SQ_FORCE_SMEM") == "1"
+                              else "first form, vectors in global scratch (SQ_FORCE_KERNEL=legacy)"
+                              if os.environ.get("SQ_FORCE_KERNEL") == "legacy"
+                              else "region form (the region kernels' recurrence with D in global scratch)"),
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "single GPU"},
         "forces_max_abs": float(F.abs().max().item()),
-        "roofline": {"kernel": "nl_force_kernel", "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
+        "roofline": {"kernel": ("nl_force_kernel" if os.environ.get("SQ_FORCE_KERNEL") == "legacy"
+                                else "force_region_kernel"),
+                     "bound": "alu", "achieved": flops / t / 1e12, "peak": peak,
                      "unit": "TFLOP/s", "frac": flops / t / 1e12 / peak, "traffic": None, "peak_basis": basis},
         "e2e": {"value": units / float(np.median(e2e)), "unit": FORCE_UNIT,
                 "h2d_bytes_per_step": 3 * wl.n_nodes * 8, "d2h_bytes_per_step": wl.n_atoms * 3 * 8},

@@ -17,7 +17,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libsq.so")
 SOURCES = ["sq_api.cu", "sq_kernels.cu", "sq_region_f32.cu", "sq_region_f64.cu", "sq_queue_f32.cu", "sq_queue_f64.cu",
            "sq_cluster_lo.cu", "sq_cluster_hi.cu",
-           "sq_noalloc.cu", "sq_scf.cu",
+           "sq_noalloc.cu", "sq_scf.cu", "sq_force_region_f32.cu", "sq_force_region_f64.cu",
            "sq_force.cu", "sq_cnn.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

@@ -236,37 +236,6 @@ int setup_projectors(sq_ctx* c, const double* xyz)
     return e == cudaSuccess ? SQ_OK : SQ_ECUDA;
 }
 
-template <typename T>
-RegionArgs<T> region_args(sq_ctx* c)
-{
-    RegionArgs<T> a;
-    memset(&a, 0, sizeof(a));
-    a.g = c->g;
-    for (int d = 0; d <= FD_NO; ++d) a.wd[d] = (T)(-0.5 * c->g.w[d]);
-    a.Vp = (const T*)c->Vp;
-    a.nl.n_atoms = (c->has_s || c->has_p) ? c->n_atoms : 0;
-    a.nl.atoms = c->d_atoms;
-    a.nl.G = (const T*)c->d_G;
-    a.nl.DG = (const T*)c->d_DG;
-    a.nl.ivl = c->d_ivl;
-    a.nl.lb = c->lb;
-    a.nl.ccap = c->ccap;
-    a.nl.smem = c->nl_mode;
-    a.nl.tile_start = c->d_tile_start;
-    a.nl.tile_cand = c->d_tile_cand;
-    for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
-    const double h3 = c->g.h * c->g.h * c->g.h;
-    const double As2 = pow(M_PI * c->rc * c->rc, -1.5);          // A_s^2
-    const double Ap2 = 2.0 / (c->rc * c->rc) * As2;              // A_p^2
-    a.nl.cs = (T)(c->has_s ? h3 * c->gamma_s * As2 : 0.0);
-    a.nl.cp = (T)(c->has_p ? h3 * c->gamma_p * Ap2 : 0.0);
-    a.scratch = (char*)c->d_scratch;
-    a.scratch_stride = c->scratch_bytes_per_cta;
-    a.err = c->d_err;
-    a.npl = c->npl;
-    a.mom_tol = c->precision == SQ_FP32 ? 1e-4 : 1e-6;
-    return a;
-}
 
 // FP32 cluster kernels (sq_cluster.cuh) for this context when
 // SQ_REGION_KERNEL=cluster is set in the environment, its region size has

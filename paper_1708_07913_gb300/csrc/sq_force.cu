@@ -1,6 +1,10 @@
 // sq_force.cu -- host side of sq_nl_forces (include/sq.h): argument checks,
-// the per-context force workspace, and the two launches (the per-node force
-// kernel of sq_force.cuh and the fixed-order sum over its CTAs).
+// the per-context force workspace, and the two launches: a per-node force
+// kernel (by default the region form of sq_force_region.cuh, which runs the
+// recurrence on the region kernels' machinery; the first form of
+// sq_force.cuh where the region form does not fit, or with
+// SQ_FORCE_KERNEL=legacy in the environment) and the fixed-order sum over
+// its CTAs.
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
@@ -12,11 +16,16 @@
 #include <vector>
 
 #include "sq_force.cuh"
+#include "sq_force_region.cuh"
 
 using namespace sq;
 
 namespace sq {
 int launch_build_vpad(sq_ctx* ctx, const double* V);
+int force_region_config_f32(int m, size_t extra, int* bps, size_t* smem);
+int force_region_config_f64(int m, size_t extra, int* bps, size_t* smem);
+int force_region_launch_f32(int m, const ForceRegionArgs<float>& f, size_t extra, int blocks, cudaStream_t st);
+int force_region_launch_f64(int m, const ForceRegionArgs<double>& f, size_t extra, int blocks, cudaStream_t st);
 }
 
 // Per-context scratch of the force kernel (created on first use, grown when
@@ -176,6 +185,103 @@ int launch_force(sq_ctx* c, const ForceLayout& L, char* base, int blocks, bool i
     return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;
 }
 
+// Per-CTA slices of the region form: D (S^3 in T), the (candidate, axis)
+// contributions of one node, the CTA's force array.
+struct RegionForceLayout {
+    size_t D, fpart, F, total;
+};
+
+RegionForceLayout region_force_layout(int S, int n_atoms, size_t tsz)
+{
+    RegionForceLayout L;
+    L.D = 0;
+    L.fpart = align256(tsz * (size_t)S * S * S);
+    L.F = L.fpart + align256(sizeof(double) * 3 * MAX_CAND);
+    L.total = L.F + align256(sizeof(double) * 3 * (size_t)n_atoms);
+    return L;
+}
+
+// Grid of the region form (0: not available for this context).
+int region_force_blocks(sq_ctx* c, long long nq, size_t* extra)
+{
+    if (c->cl_nc > 0 || !c->d_scratch) return 0;        // the cluster kernels keep no per-CTA scratch
+    const char* env = getenv("SQ_FORCE_KERNEL");
+    if (env && strcmp(env, "legacy") == 0) return 0;
+    *extra = force_coef_bytes(c->npl) + c->nl_extra;
+    int bps = 0;
+    size_t smem = 0;
+    const int rc = c->precision == SQ_FP32 ? force_region_config_f32(c->g.m, *extra, &bps, &smem)
+                                           : force_region_config_f64(c->g.m, *extra, &bps, &smem);
+    if (rc || bps < 1) return 0;
+    long long b = std::min<long long>((long long)bps * c->sm_count, c->grid_blocks);
+    return (int)std::min<long long>(b, nq);
+}
+
+int force_region_launch(int m, const ForceRegionArgs<float>& f, size_t extra, int blocks, cudaStream_t st)
+{
+    return force_region_launch_f32(m, f, extra, blocks, st);
+}
+int force_region_launch(int m, const ForceRegionArgs<double>& f, size_t extra, int blocks, cudaStream_t st)
+{
+    return force_region_launch_f64(m, f, extra, blocks, st);
+}
+
+template <typename T>
+int launch_force_region(sq_ctx* c, const RegionForceLayout& L, char* base, int blocks, size_t extra,
+                        const double* chi, const double* zeta, double mu, double kT, const long long* nodes,
+                        long long nq, double* forces)
+{
+    ForceRegionArgs<T> f;
+    memset(&f, 0, sizeof(f));
+    f.r = region_args<T>(c);
+    f.r.chi = chi;
+    f.r.zeta = zeta;
+    grad_weights(FD_NO, c->g.h, f.grad);
+    f.mu = mu;
+    f.kT = kT;
+    f.nodes = nodes;
+    f.nq = nq;
+    f.D = (T*)(base + L.D * blocks);
+    f.fpart = (double*)(base + L.fpart * blocks);
+    f.Fcta = (double*)(base + L.F * blocks);
+    int rc = force_region_launch(c->g.m, f, extra, blocks, c->stream);
+    if (rc) return rc;
+    const int n3 = 3 * c->n_atoms;
+    force_sum_kernel<<<(n3 + 127) / 128, 128, 0, c->stream>>>(f.Fcta, blocks, n3, forces);
+    return cudaGetLastError() == cudaSuccess ? SQ_OK : SQ_ECUDA;
+}
+
+// The context's force workspace, at least `need` bytes.
+int force_workspace(sq_ctx* c, size_t need, ForceWS** out)
+{
+    ForceWS* ws = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_force_mutex);
+        auto it = g_force_ws.find(c);
+        if (it != g_force_ws.end()) ws = it->second;
+    }
+    if (!ws || ws->bytes < need) {
+        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
+        std::lock_guard<std::mutex> lk(g_force_mutex);
+        auto it = g_force_ws.find(c);
+        if (it != g_force_ws.end()) {
+            ws_release(it->second);
+            g_force_ws.erase(it);
+        }
+        ws = new (std::nothrow) ForceWS();
+        if (!ws) return SQ_ENOMEM;
+        if (cudaMalloc((void**)&ws->buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            ws_release(ws);
+            return SQ_ENOMEM;
+        }
+        ws->bytes = need;
+        g_force_ws[c] = ws;
+    }
+    *out = ws;
+    return SQ_OK;
+}
+
 }  // namespace
 
 namespace sq {
@@ -218,44 +324,31 @@ int nl_forces(sq_ctx* c, const double* V, const double* chi, const double* zeta,
 
     const int S = 2 * c->g.m + 1;
     const size_t tsz = c->precision == SQ_FP32 ? sizeof(float) : sizeof(double);
-    const ForceLayout L = force_layout(S, c->ccap, c->n_atoms, tsz);
-    bool inplace = true;
-    size_t dyn = 0;
-    int blocks = 0;
-    int rcc = c->precision == SQ_FP32 ? force_config<float>(c, nq, &inplace, &dyn, &blocks)
-                                      : force_config<double>(c, nq, &inplace, &dyn, &blocks);
-    if (rcc) return rcc;
-    const size_t need = L.total * (size_t)blocks;
     ForceWS* ws = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_force_mutex);
-        auto it = g_force_ws.find(c);
-        if (it != g_force_ws.end()) ws = it->second;
+    int rc;
+    size_t extra = 0;
+    const int rblocks = region_force_blocks(c, nq, &extra);
+    if (rblocks > 0) {
+        const RegionForceLayout L = region_force_layout(S, c->n_atoms, tsz);
+        if ((rc = force_workspace(c, L.total * (size_t)rblocks, &ws))) return rc;
+        if ((rc = launch_build_vpad(c, V))) return rc;
+        rc = c->precision == SQ_FP32
+                 ? launch_force_region<float>(c, L, ws->buf, rblocks, extra, chi, zeta, mu, kT, nodes, nq, forces)
+                 : launch_force_region<double>(c, L, ws->buf, rblocks, extra, chi, zeta, mu, kT, nodes, nq, forces);
+    } else {
+        const ForceLayout L = force_layout(S, c->ccap, c->n_atoms, tsz);
+        bool inplace = true;
+        size_t dyn = 0;
+        int blocks = 0;
+        int rcc = c->precision == SQ_FP32 ? force_config<float>(c, nq, &inplace, &dyn, &blocks)
+                                          : force_config<double>(c, nq, &inplace, &dyn, &blocks);
+        if (rcc) return rcc;
+        if ((rc = force_workspace(c, L.total * (size_t)blocks, &ws))) return rc;
+        if ((rc = launch_build_vpad(c, V))) return rc;
+        rc = c->precision == SQ_FP32
+                 ? launch_force<float>(c, L, ws->buf, blocks, inplace, dyn, chi, zeta, mu, kT, nodes, nq, forces)
+                 : launch_force<double>(c, L, ws->buf, blocks, inplace, dyn, chi, zeta, mu, kT, nodes, nq, forces);
     }
-    if (!ws || ws->bytes < need) {
-        if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;
-        std::lock_guard<std::mutex> lk(g_force_mutex);
-        auto it = g_force_ws.find(c);
-        if (it != g_force_ws.end()) {
-            ws_release(it->second);
-            g_force_ws.erase(it);
-        }
-        ws = new (std::nothrow) ForceWS();
-        if (!ws) return SQ_ENOMEM;
-        if (cudaMalloc((void**)&ws->buf, need) != cudaSuccess) {
-            cudaGetLastError();
-            ws_release(ws);
-            return SQ_ENOMEM;
-        }
-        ws->bytes = need;
-        g_force_ws[c] = ws;
-    }
-
-    int rc = launch_build_vpad(c, V);
-    if (rc) return rc;
-    rc = c->precision == SQ_FP32
-             ? launch_force<float>(c, L, ws->buf, blocks, inplace, dyn, chi, zeta, mu, kT, nodes, nq, forces)
-             : launch_force<double>(c, L, ws->buf, blocks, inplace, dyn, chi, zeta, mu, kT, nodes, nq, forces);
     if (rc) return rc;
     c->launches += 2;
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return SQ_ECUDA;

@@ -17,6 +17,9 @@
 // to the first when both fit (FP32 regions up to 25^3, FP64 up to 19^3), and
 // in per-CTA global scratch otherwise.
 #pragma once
+#include <math.h>
+#include <string.h>
+
 #include "sq_internal.cuh"
 
 namespace sq {
@@ -180,6 +183,39 @@ struct RegionArgs {
     double* beta;
     int* klen;
 };
+
+// The region-kernel arguments of a context (host).
+template <typename T>
+inline RegionArgs<T> region_args(const sq_ctx* c)
+{
+    RegionArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.g = c->g;
+    for (int d = 0; d <= FD_NO; ++d) a.wd[d] = (T)(-0.5 * c->g.w[d]);
+    a.Vp = (const T*)c->Vp;
+    a.nl.n_atoms = (c->has_s || c->has_p) ? c->n_atoms : 0;
+    a.nl.atoms = c->d_atoms;
+    a.nl.G = (const T*)c->d_G;
+    a.nl.DG = (const T*)c->d_DG;
+    a.nl.ivl = c->d_ivl;
+    a.nl.lb = c->lb;
+    a.nl.ccap = c->ccap;
+    a.nl.smem = c->nl_mode;
+    a.nl.tile_start = c->d_tile_start;
+    a.nl.tile_cand = c->d_tile_cand;
+    for (int i = 0; i < 3; ++i) a.nl.ntile[i] = c->ntile[i];
+    const double h3 = c->g.h * c->g.h * c->g.h;
+    const double As2 = pow(M_PI * c->rc * c->rc, -1.5);          // A_s^2
+    const double Ap2 = 2.0 / (c->rc * c->rc) * As2;              // A_p^2
+    a.nl.cs = (T)(c->has_s ? h3 * c->gamma_s * As2 : 0.0);
+    a.nl.cp = (T)(c->has_p ? h3 * c->gamma_p * Ap2 : 0.0);
+    a.scratch = (char*)c->d_scratch;
+    a.scratch_stride = c->scratch_bytes_per_cta;
+    a.err = c->d_err;
+    a.npl = c->npl;
+    a.mom_tol = c->precision == SQ_FP32 ? 1e-4 : 1e-6;
+    return a;
+}
 
 template <typename T>
 __device__ inline CtaScratch<T> cta_scratch(const RegionArgs<T>& a, int m)
@@ -870,9 +906,11 @@ __device__ void nl_update_red(const RegionArgs<T>& a, const CtaScratch<T>& sc, T
 // RECUR = false (Lanczos): out = w goes to sec; t is left in place; the
 //   thread accumulates out.out, out.t and t.t.
 // ------------------------------------------------------------------------
-template <typename T, int M, bool RECUR, bool DB, bool YEDGE = false>
+// ACCD (recurrence only): also D += cd * t^{i+1} at every point, D being an
+// unpadded S^3 array (x fastest) that only the point's own thread touches.
+template <typename T, int M, bool RECUR, bool DB, bool YEDGE = false, bool ACCD = false>
 __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* vwin, T s, T dshift,
-                              T& acc_a, T& acc_b, T& acc_c, double* centre_out)
+                              T& acc_a, T& acc_b, T& acc_c, double* centre_out, T* D = nullptr, T cd = T(0))
 {
     using G = Geo<M>;
     using SV = Sec<M, DB>;
@@ -933,6 +971,7 @@ __device__ void stencil_sweep(const RegionArgs<T>& a, T* cur, T* sec, const T* v
                 aa += out * out;
                 ab += out * c;
                 if (x == M && y == M && z == M) *centre_out = (double)out;
+                if constexpr (ACCD) D[((size_t)z * G::S + y) * G::S + x] += cd * out;
             } else {
                 bcol[z * SV::ZS] = out;
                 aa += out * out;

@@ -66,17 +66,24 @@ CASES = {
 }
 
 
-@pytest.mark.parametrize("form", ["global", "smem"])
+def _form(monkeypatch, form):
+    """The force kernel the library uses for the next call: the region form
+    (the default), or the first form with every vector in global scratch
+    (SQ_FORCE_KERNEL=legacy) or with the current vector in shared memory
+    (and SQ_FORCE_SMEM=1); both variables are read at each call."""
+    monkeypatch.delenv("SQ_FORCE_KERNEL", raising=False)
+    monkeypatch.delenv("SQ_FORCE_SMEM", raising=False)
+    if form != "region":
+        monkeypatch.setenv("SQ_FORCE_KERNEL", "legacy")
+    if form == "legacy_smem":
+        monkeypatch.setenv("SQ_FORCE_SMEM", "1")
+
+
+@pytest.mark.parametrize("form", ["region", "legacy_global", "legacy_smem"])
 @pytest.mark.parametrize("precision", [SQ_FP64, SQ_FP32])
 @pytest.mark.parametrize("name", list(CASES))
 def test_nl_forces_match_oracle(name, precision, form, monkeypatch):
-    """Both storage forms of the force kernel: every vector in global scratch
-    (the default), and the current vector in shared memory (SQ_FORCE_SMEM=1),
-    read by the library at each call."""
-    if form == "smem":
-        monkeypatch.setenv("SQ_FORCE_SMEM", "1")
-    else:
-        monkeypatch.delenv("SQ_FORCE_SMEM", raising=False)
+    _form(monkeypatch, form)
     wl, s, pt = _system(**CASES[name])
     osys = oracle.OracleSystem(s.V, wl.h, wl.m, s.positions, pt)
     nodes = np.arange(wl.n_nodes)
@@ -94,10 +101,10 @@ def test_nl_forces_match_oracle(name, precision, form, monkeypatch):
     solver.close()
 
 
-@pytest.mark.parametrize("name,precision,count,form", [("al108_48", SQ_FP64, 16, "global"),
-                                                       ("al108_48", SQ_FP32, 16, "global"),
-                                                       ("al108_48", SQ_FP32, 16, "smem"),
-                                                       ("al2048_128", SQ_FP32, 6, "global")])
+@pytest.mark.parametrize("name,precision,count,form", [("al108_48", SQ_FP64, 16, "region"),
+                                                       ("al108_48", SQ_FP32, 16, "region"),
+                                                       ("al108_48", SQ_FP32, 16, "legacy_global"),
+                                                       ("al2048_128", SQ_FP32, 6, "region")])
 def test_nl_forces_full_size_sampled_nodes(name, precision, count, form, monkeypatch):
     """Full-size workloads: al108_48 (the benchmark workload: 25^3 regions,
     n_pl 48, 108 atoms) and al2048_128 (the scale workload: 128^3 grid, 29^3
@@ -105,10 +112,7 @@ def test_nl_forces_full_size_sampled_nodes(name, precision, count, form, monkeyp
     The force contributions of seeded nodes on the benchmark's launch
     configuration, against the oracle on the same nodes (the oracle's bounds
     and Fermi level on the GPU side)."""
-    if form == "smem":
-        monkeypatch.setenv("SQ_FORCE_SMEM", "1")
-    else:
-        monkeypatch.delenv("SQ_FORCE_SMEM", raising=False)
+    _form(monkeypatch, form)
     s = synth.make_system(name)
     wl = s.wl
     nodes = synth.sample_nodes(wl.n_nodes, count, seed=31)
