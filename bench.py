@@ -73,6 +73,8 @@ def parse():
     p.add_argument("--margin", type=float, default=0.0,
                    help="with --n-lanczos: the bounds' relative widening (0: the workload's)")
     p.add_argument("--save-rho", default="", help="write the last step's density (float32 .npy) to this path")
+    p.add_argument("--fresh-below", default="none",
+                   help="scf_*, warmstart_c4: residual below which bounds are no longer reused (none: reuse to the end)")
     p.add_argument("--refine-at", default="none",
                    help="scf_*, warmstart_c4: residual at which an FP64 context takes over (none: FP32 throughout)")
     p.add_argument("--batch-plan", choices=["auto", "streams", "share", "queue"], default="auto",
@@ -810,8 +812,9 @@ def run_scf(a):
     refine_at = None if a.refine_at == "none" else float(a.refine_at)
     if refine_at is not None:
         fine = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=str(dev))
+    fresh = None if a.fresh_below == "none" else float(a.fresh_below)
     scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=a.beta, history=a.history, margin=wl.margin,
-                kerker=kerker, period=a.period, reuse_bounds=reuse,
+                kerker=kerker, period=a.period, reuse_bounds=reuse, fresh_below=fresh,
                 refine=None if fine is None else (fine, refine_at))
     solver.solve(V_loc, wl.n_electrons, wl.kT, wl.n_lanczos, wl.margin)      # warm-up (not timed)
     torch.cuda.synchronize()
@@ -839,7 +842,7 @@ def run_scf(a):
         "config": {"workload": f"{a.workload}: {wl.cells}^3 cells ({wl.n_atoms} atoms), {wl.n}^3 grid, "
                                f"{2 * wl.m + 1}^3 regions, n_pl={wl.npl}, kT={wl.kT}",
                    "mixing": {"beta": a.beta, "history": a.history, "period": a.period, "kerker": kerker},
-                   "reuse_bounds": reuse, "fp64_from_residual": refine_at,
+                   "reuse_bounds": reuse, "fresh_bounds_below": fresh, "fp64_from_residual": refine_at,
                    "tolerance": 1e-6, "parallelism": "single GPU"},
         "iterations": it, "converged": out["converged"], "residuals": [float(r) for r in out["residuals"]],
         "lanczos_runs": out["lanczos_runs"], "fp64_from_iteration": out["refined_at"],
@@ -886,8 +889,9 @@ def run_warmstart(a):
         nets[label] = (net, fermi)
     reuse = None if a.reuse_bounds == "none" else float(a.reuse_bounds)
     refine_at = None if a.refine_at == "none" else float(a.refine_at)
+    fresh = None if a.fresh_below == "none" else float(a.fresh_below)
     res = wsm.compare(nets, target, tol=1e-6, max_iter=a.max_scf, device=str(dev), reuse_bounds=reuse,
-                      refine_at=refine_at)
+                      fresh_below=fresh, refine_at=refine_at)
     clk = clocks.stop()
     for net, _ in nets.values():
         net.close()
@@ -904,7 +908,7 @@ def run_warmstart(a):
                    "fermi_level_offsets": [-0.1, -0.05, 0.0, 0.05, 0.1],
                    "scf_iterations_per_geometry": a.train_iters, "adam_steps": a.train_steps,
                    "mixing": "Anderson, history 16, beta 0.3, Kerker (0.5, 0.1)", "best": best,
-                   "reuse_bounds": reuse, "fp64_from_residual": refine_at,
+                   "reuse_bounds": reuse, "fresh_bounds_below": fresh, "fp64_from_residual": refine_at,
                    "parallelism": "single GPU"},
         "plain_iterations": res["plain"]["iterations"], "plain_converged": res["plain"]["converged"],
         "results": res,

@@ -179,7 +179,7 @@ class SQSCF:
     sequences them."""
 
     def __init__(self, solver, V_loc, n_electrons, kT, alpha=2.0 / 3.0, beta=0.3, history=7, n_lanczos=40,
-                 margin=0.01, kerker=None, period=1, reuse_bounds=None, refine=None):
+                 margin=0.01, kerker=None, period=1, reuse_bounds=None, fresh_below=None, refine=None):
         """``kerker`` = (k0, amin): mix the Kerker-preconditioned residual
         (sq_kerker) in place of V_out - V_in; the stopping test stays on the
         unpreconditioned residual.  ``period`` = p > 1: Periodic Pulay
@@ -192,18 +192,25 @@ class SQSCF:
         the SQ map the mixer iterates no longer changes with the rounding of
         fresh bounds (in FP32 that rounding moves zeta by ~1e-5 relative and
         puts a floor under the residual); the fixed point is that of SQ with
-        those enclosing bounds, at most w_max wider than fresh ones.
+        those enclosing bounds, at most w_max wider than fresh ones -- and at
+        low degree the SQ density moves noticeably with the bounds, so
+        ``fresh_below`` = r ends the reuse once the residual is at or below
+        r: from then on every iteration takes fresh bounds, and the loop ends
+        on the fixed point of SQ with bounds of (nearly) its own potential.
         ``refine`` = (solver_fp64, r_switch): once the residual is at or below
         r_switch, the remaining iterations run on solver_fp64 (an FP64
         context of the same grid and atoms), starting from the current bounds
-        and keeping the mixing history.  The FP32 recurrence leaves rounding
-        noise of ~1e-6 relative in the density, which stalls the residual
-        near that level; the FP64 iterations converge past it."""
+        and keeping the mixing history; they reuse the last Lanczos bounds
+        widened by the potential change while that stays within 1e-3 Ha (an
+        FP64 Lanczos run costs about two FP64 SQ steps).  The FP32 recurrence
+        leaves rounding noise of ~1e-6 relative in the density, which stalls
+        the residual near that level; the FP64 iterations converge past it."""
         torch = solver.torch
         self.solver, self.V_loc = solver, V_loc
         self.kerker = None if kerker is None else (float(kerker[0]), float(kerker[1]))
         self.period = int(period)
         self.reuse = None if reuse_bounds is None else float(reuse_bounds)
+        self.fresh_below = None if fresh_below is None else float(fresh_below)
         self.refine = None if refine is None else (refine[0], float(refine[1]))
         self.n_electrons, self.kT, self.alpha = float(n_electrons), float(kT), float(alpha)
         self.n_lanczos, self.margin = int(n_lanczos), float(margin)
@@ -246,18 +253,22 @@ class SQSCF:
                 fine.chi.copy_(sv.chi)
                 fine.zeta.copy_(sv.zeta)
                 sv, refined_at = fine, it
-                if ref is None:                      # without bound reuse: keep these bounds as the reference
-                    ref = (V_in.clone(), sv.chi.clone(), sv.zeta.clone())
+            if refined_at is not None:
+                w_max = 1e-3
+            elif self.reuse is not None and not (self.fresh_below is not None and res and res[-1] <= self.fresh_below):
+                w_max = self.reuse
+            else:
+                w_max = None                         # fresh bounds this iteration
             widened = False
-            if ref is not None and (self.reuse is not None or refined_at is not None):
+            if ref is not None and w_max is not None:
                 w = sv.widen_bounds(V_in, *ref)
-                widened = w <= (self.reuse if self.reuse is not None else 0.05)
+                widened = w <= w_max
             if widened:
                 out = sv.solve(V_in, self.n_electrons, self.kT, bounds=(sv.chi, sv.zeta))
             else:
                 out = sv.solve(V_in, self.n_electrons, self.kT, self.n_lanczos, self.margin)
                 lanczos += 1
-                if self.reuse is not None or refined_at is not None:
+                if self.reuse is not None or self.refine is not None:
                     ref = (V_in.clone(), sv.chi.clone(), sv.zeta.clone())
             if on_step is not None:
                 on_step(V_in, sv.rho, out["mu"])

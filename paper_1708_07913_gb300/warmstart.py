@@ -100,16 +100,16 @@ def train(net, pairs, steps, batch=8, lr=2e-3, lr_final=2e-4, seed=0, log_every=
 
 
 def compare(nets, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0", beta=0.3, history=16,
-            kerker=(0.5, 0.1), reuse_bounds=None, refine_at=None):
+            kerker=(0.5, 0.1), reuse_bounds=None, fresh_below=None, refine_at=None):
     """SCF iterations of ``wl`` from V_loc and from the warm start of each
     network in ``nets`` = {label: (net, fermi_referenced)}, all with the same
     mixer (Kerker-preconditioned unless ``kerker`` is None).  Returns
     {"plain": {...}, label: {...}} with iterations, convergence, residual
     histories, times, and for the warm starts the surrogate's steps and
     residual, whether the network's potential was kept, and the largest
-    density difference to the plain SCF's fixed point.  ``reuse_bounds`` and
-    ``refine_at`` (an FP64 context takes over at that residual) are passed
-    to SQSCF."""
+    density difference to the plain SCF's fixed point.  ``reuse_bounds``,
+    ``fresh_below`` and ``refine_at`` (an FP64 context takes over at that
+    residual) are passed to SQSCF."""
     import torch
     s = synth.make_system(wl)
     solver = SQSolver.from_workload(wl, s.positions, precision=precision, device=device)
@@ -118,7 +118,8 @@ def compare(nets, wl, tol=1e-6, max_iter=100, precision=SQ_FP32, device="cuda:0"
         fine = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=device)
     V_loc = torch.from_numpy(s.V.ravel().copy()).to(device)
     scf = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, beta=beta, history=history, margin=wl.margin, kerker=kerker,
-                reuse_bounds=reuse_bounds, refine=None if fine is None else (fine, refine_at))
+                reuse_bounds=reuse_bounds, fresh_below=fresh_below,
+                refine=None if fine is None else (fine, refine_at))
     t0 = time.perf_counter()
     plain = scf.run(tol=tol, max_iter=max_iter)
     out = {"plain": dict(iterations=plain["iterations"], converged=plain["converged"],
