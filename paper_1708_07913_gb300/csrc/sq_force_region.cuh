@@ -19,8 +19,10 @@
 // axis) contracts chi_p with the gradient of D over the candidate's support,
 // lanes over the points of each support row, FP64 sums reduced in a fixed
 // tree; thread 0 adds the node's contributions to a per-CTA force array in
-// candidate order, and force_sum_kernel adds the CTA arrays in block order,
-// so the result repeats bit for bit.
+// candidate order, and force_sum_kernel adds the CTA arrays in block order.
+// The FP64 result repeats bit for bit; in FP32 the projector update adds
+// with shared-memory atomics (as in the moments kernel), so repeated runs
+// differ at the rounding level.
 #pragma once
 #include "sq_region.cuh"
 
@@ -116,13 +118,10 @@ __device__ void force_node(const ForceRegionArgs<T>& f, unsigned char* smem_raw,
         const T s = (i == 0) ? s1 : s2;
         nl_dots<T, M>(a, sc, cur, ncand);
         __syncthreads();
-        if constexpr (sizeof(T) == 4) {
-            nl_update_red<T, M, DB>(a, sc, sec, ncand, s);
-        } else {
-            nl_collect<T, M>(sc, ncand);
-            __syncthreads();
-            nl_update<T, M, DB>(a, sc, sec, s);
-        }
+        nl_collect<T, M>(sc, ncand);
+        __syncthreads();
+        if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, s);
+        else nl_update<T, M, DB>(a, sc, sec, s);
         __syncthreads();
         const T cd = (T)s_c[i + 1];
         T u0, u1, u2;

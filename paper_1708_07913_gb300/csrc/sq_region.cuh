@@ -95,9 +95,6 @@ struct ScratchLayout {
 };
 __host__ __device__ inline size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 __host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
-// Box columns per candidate in the x-tables: lb rounded up to even, so that
-// the (G, DG) pairs of slots 2h and 2h+1 are one 16-byte load in FP32.
-__host__ __device__ inline int tx_stride(int lb) { return (lb + 1) & ~1; }
 __host__ __device__ inline size_t rec_size(size_t tsize) { return tsize == 4 ? 16 : 32; }   // sizeof(EntRec<T>)
 __host__ __device__ inline ScratchLayout scratch_layout(int m, size_t tsize)
 {
@@ -123,10 +120,9 @@ __host__ __device__ inline ScratchLayout scratch_layout(int m, size_t tsize)
 // Shared-memory placement of the per-candidate tables for ccap candidates
 // with x-tables of lb box columns (offsets from a 16-byte aligned base; total
 // includes 16 bytes of slack for aligning that base).  NL_ALL: every table;
-// NL_HOT: only those read every step (x-tables, chunk and entry offsets, and
-// in FP64 the inner products; the FP32 update sums them from the partials),
-// the rest staying in global scratch, for regions whose vectors leave too
-// little room for all of them.
+// NL_HOT: only those read every step (inner products, x-tables, chunk and
+// entry offsets), the rest staying in global scratch, for regions whose
+// vectors leave too little room for all of them.
 enum : int { NL_GLOBAL = 0, NL_ALL = 1, NL_HOT = 2 };
 struct NLSmem {
     size_t cand, P, TX, seg, clen, cand_start, chunk_first, row_n, total;
@@ -135,11 +131,8 @@ __host__ __device__ inline NLSmem nl_smem_layout(int mode, int ccap, int S, int 
 {
     NLSmem L;
     size_t o = 0;
-    L.P = 0;
-    if (mode == NL_ALL || tsize == 8) {
-        L.P = o;       o = align16(o + (size_t)ccap * 4 * tsize);
-    }
-    L.TX = o;          o = align16(o + (size_t)ccap * 2 * tx_stride(lb) * tsize);
+    L.P = o;           o = align16(o + (size_t)ccap * 4 * tsize);
+    L.TX = o;          o = align16(o + (size_t)ccap * 2 * lb * tsize);
     L.cand_start = o;  o = align16(o + (size_t)(ccap + 1) * sizeof(int));
     L.chunk_first = o; o = align16(o + (size_t)(ccap + 1) * sizeof(int));
     L.cand = L.seg = L.clen = L.row_n = 0;
@@ -244,7 +237,7 @@ __device__ inline void nl_tables_in_smem(CtaScratch<T>& s, void* p_, int mode, i
 {
     char* p = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(p_) + 15) & ~uintptr_t(15));
     const NLSmem L = nl_smem_layout(mode, ccap, S, lb, sizeof(T));
-    if (mode == NL_ALL || sizeof(T) == 8) s.P = reinterpret_cast<T*>(p + L.P);
+    s.P = reinterpret_cast<T*>(p + L.P);
     s.TX = reinterpret_cast<T*>(p + L.TX);
     s.cand_start = reinterpret_cast<int*>(p + L.cand_start);
     s.chunk_first = reinterpret_cast<int*>(p + L.chunk_first);
@@ -423,13 +416,12 @@ __device__ int nl_setup(const RegionArgs<T>& a, const CtaScratch<T>& sc, int qi,
     if (ncand > lim) ncand = lim;
     for (int c = tid; c <= ncand; c += G::NT) sc.cand_start[c] = 0;     // entry counts first
     __syncthreads();
-    // (2) x-tables of the candidates by box column k (tx_stride(lb) per
-    // candidate; zero beyond the box)
-    const int lbp = tx_stride(lb);
-    for (int i = tid; i < ncand * lbp; i += G::NT) {
-        const int c = i / lbp, k = i % lbp;
+    // (2) x-tables of the candidates by box column k (lb per candidate; zero
+    // beyond the box)
+    for (int i = tid; i < ncand * lb; i += G::NT) {
+        const int c = i / lb, k = i % lb;
         T g = 0, dg = 0;
-        if (k < min(sc.clen[c] & 255, lb)) {
+        if (k < (sc.clen[c] & 255)) {
             const int atom = sc.cand[c].x;
             g = nl.G[(size_t)atom * 3 * lb + k];
             dg = nl.DG[(size_t)atom * 3 * lb + k];
@@ -600,38 +592,19 @@ __device__ void nl_dots(const RegionArgs<T>& a, const CtaScratch<T>& sc, const T
             // slots k of the candidate's box, x = bx + k: every lane of the
             // chunk reads the same (G, DG) pair, and rows of one plane sit in
             // distinct banks
-            const P2* txp = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * tx_stride(lb);
+            const P2* txp = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * lb;
             const T* rowp = row + bx;
             T u = 0, u2 = 0;
             if (unrolled) {
                 const uint32_t mask = ((2u << (xhi - bx)) - 1u) & ~((1u << (xlo - bx)) - 1u);
-                if constexpr (sizeof(T) == 4) {       // slot pairs: one 16-byte broadcast load per two slots
-                    const float4* tx4 = reinterpret_cast<const float4*>(txp);
 #pragma unroll
-                    for (int h = 0; h < LBMAX / 2; ++h)
-                        if (mask & (3u << (2 * h))) {
-                            const float4 g = tx4[h];
-                            if (mask & (1u << (2 * h))) {
-                                const T tv = rowp[2 * h];
-                                u += g.x * tv;
-                                u2 += g.y * tv;
-                            }
-                            if (mask & (2u << (2 * h))) {
-                                const T tv = rowp[2 * h + 1];
-                                u += g.z * tv;
-                                u2 += g.w * tv;
-                            }
-                        }
-                } else {
-#pragma unroll
-                    for (int k = 0; k < LBMAX; ++k)
-                        if (mask & (1u << k)) {
-                            const P2 g = txp[k];
-                            const T tv = rowp[k];
-                            u += g.x * tv;
-                            u2 += g.y * tv;
-                        }
-                }
+                for (int k = 0; k < LBMAX; ++k)
+                    if (mask & (1u << k)) {
+                        const P2 g = txp[k];
+                        const T tv = rowp[k];
+                        u += g.x * tv;
+                        u2 += g.y * tv;
+                    }
             } else {
                 for (int k = xlo - bx; k <= xhi - bx; ++k) {
                     const P2 g = txp[k];
@@ -753,7 +726,7 @@ __device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* se
         load_P<T>(sc.P, c, pS, pX, pY, pZ);
         const T b0 = cs * rc.f0 * pS + cp * (rc.f1 * pY + rc.f2 * pZ);
         const T b1 = cp * rc.f0 * pX;
-        const P2* tx = tx2 + (size_t)c * tx_stride(a.nl.lb) + (xlo - bx);
+        const P2* tx = tx2 + (size_t)c * a.nl.lb + (xlo - bx);
         T* bp = brow + xlo;
         const int len = xhi - xlo;                    // slots 0..len
         bool done = false;
@@ -790,10 +763,7 @@ __device__ void nl_update(const RegionArgs<T>& a, const CtaScratch<T>& sc, T* se
 // candidate-ordered entries exactly like nl_dots (equal runs of 32-entry
 // chunks per warp, one entry per lane, slots from the candidate's box start,
 // records two chunks ahead), and adds each point's contribution with a
-// shared-memory atomic add.  A candidate's inner products are summed from
-// the warps' partials in warp order when its first chunk comes up (the sums
-// nl_collect forms for the FP64 form, in the same order), so the FP32 step
-// needs no collection pass and no barrier for it.  Lanes of a chunk own distinct rows; points
+// shared-memory atomic add.  Lanes of a chunk own distinct rows; points
 // covered by several candidates receive their contributions in an order
 // that varies from run to run, so this form is reproducible to FP32
 // rounding rather than bitwise (the FP64 form keeps the fixed order).
@@ -831,8 +801,6 @@ __device__ void nl_update_red(const RegionArgs<T>& a, const CtaScratch<T>& sc, T
         while (j0 + 1 >= sc.chunk_first[cB + 1]) ++cB;
         fetch(j0 + 1, cB, rB, vB);
     }
-    int cP = -1;                                      // the candidate whose inner products are in hand
-    T pS = 0, pX = 0, pY = 0, pZ = 0;
     for (int j = j0; j < j1; ++j) {
         const EntRec<T> rc = rA;
         const bool val = vA;
@@ -844,43 +812,28 @@ __device__ void nl_update_red(const RegionArgs<T>& a, const CtaScratch<T>& sc, T
             while (j + 2 >= sc.chunk_first[cB + 1]) ++cB;
             fetch(j + 2, cB, rB, vB);
         }
-        if (c != cP) {                                // warp-uniform: P_c from the warps' partial sums
-            cP = c;
-            pS = pX = pY = pZ = 0;
-            const int f0 = sc.chunk_first[c], f1 = sc.chunk_first[c + 1];
-            for (int w = f0 / Q; w <= (f1 - 1) / Q; ++w) {
-                const T* sg = sc.seg + (size_t)(c + w) * 4;
-                pS += sg[0];
-                pX += sg[1];
-                pY += sg[2];
-                pZ += sg[3];
-            }
-        }
         if (!val) continue;
         const int r = rc.meta & 1023u, xlo = (rc.meta >> 10) & 31u, xhi = (rc.meta >> 15) & 31u;
         const int bx = (int)((rc.meta >> 20) & 63u) - 32;
+        T pS, pX, pY, pZ;
+        load_P<T>(sc.P, c, pS, pX, pY, pZ);
         const T b0 = cs * rc.f0 * pS + cp * (rc.f1 * pY + rc.f2 * pZ);
         const T b1 = cp * rc.f0 * pX;
         T* rowp = Sec<M, DB>::row(sec, r % G::S, r / G::S) + bx;
-        const P2* txp = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * tx_stride(lb);
+        const P2* txp = reinterpret_cast<const P2*>(sc.TX) + (size_t)c * lb;
         if (unrolled) {
             const uint32_t mask = ((2u << (xhi - bx)) - 1u) & ~((1u << (xlo - bx)) - 1u);
-            const float4* tx4 = reinterpret_cast<const float4*>(txp);   // this form is FP32 only
 #pragma unroll
-            for (int h = 0; h < LBMAX / 2; ++h)
-                if (mask & (3u << (2 * h))) {
-                    const float4 g = tx4[h];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e)
-                        if (mask & (1u << (2 * h + e))) {
-                            const T d = -((e ? g.z : g.x) * b0 + (e ? g.w : g.y) * b1);
-                            if constexpr (DB) {
-                                const unsigned addr = (unsigned)__cvta_generic_to_shared(rowp + 2 * h + e);
-                                asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(d) : "memory");
-                            } else {
-                                atomicAdd(rowp + 2 * h + e, d);
-                            }
-                        }
+            for (int k = 0; k < LBMAX; ++k)
+                if (mask & (1u << k)) {
+                    const P2 g = txp[k];
+                    const T d = -(g.x * b0 + g.y * b1);
+                    if constexpr (DB) {
+                        const unsigned addr = (unsigned)__cvta_generic_to_shared(rowp + k);
+                        asm volatile("red.shared.add.f32 [%0], %1;" ::"r"(addr), "f"(d) : "memory");
+                    } else {
+                        atomicAdd(rowp + k, d);
+                    }
                 }
         } else {
             for (int k = xlo - bx; k <= xhi - bx; ++k) {
@@ -1041,13 +994,10 @@ __device__ void moments_node(const RegionArgs<T>& a, unsigned char* smem_raw, lo
         if (has_nl) {
             nl_dots<T, M>(a, sc, cur, ncand);
             __syncthreads();
-            if constexpr (sizeof(T) == 4) {
-                nl_update_red<T, M, DB>(a, sc, sec, ncand, s);
-            } else {
-                nl_collect<T, M>(sc, ncand);
-                __syncthreads();
-                nl_update<T, M, DB>(a, sc, sec, s);
-            }
+            nl_collect<T, M>(sc, ncand);
+            __syncthreads();
+            if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, s);
+            else nl_update<T, M, DB>(a, sc, sec, s);
             __syncthreads();
         }
         T aa, ab, unused;
@@ -1144,13 +1094,10 @@ __device__ void lanczos_node(const RegionArgs<T>& a, unsigned char* smem_raw, lo
         if (has_nl) {
             nl_dots<T, M>(a, sc, sm, ncand);
             __syncthreads();
-            if constexpr (sizeof(T) == 4) {
-                nl_update_red<T, M, DB>(a, sc, sec, ncand, T(1));
-            } else {
-                nl_collect<T, M>(sc, ncand);
-                __syncthreads();
-                nl_update<T, M, DB>(a, sc, sec, T(1));
-            }
+            nl_collect<T, M>(sc, ncand);
+            __syncthreads();
+            if constexpr (sizeof(T) == 4) nl_update_red<T, M, DB>(a, sc, sec, ncand, T(1));
+            else nl_update<T, M, DB>(a, sc, sec, T(1));
             __syncthreads();
         }
         T ww, vw, vv;

@@ -5,6 +5,10 @@ potential.
 
 Tolerance: FP64, the same arithmetic in another summation order over a
 recurrence of n_pl steps: 1e-10 of the largest force component, absolute.
+Three kernel forms are run: the region form (the region kernels'
+recurrence, the default; in FP32 its projector update adds with shared-
+memory atomics, so its repeats agree to rounding rather than bit for bit)
+and the first form with its vectors in global scratch or in shared memory.
 FP32 context (recurrence, D and projector sums in FP32; coefficients and
 contraction in FP64): 1e-4 of the largest component.  The rounding error of
 the FP32 recurrence grows with the degree; the same arithmetic run on the
@@ -97,7 +101,10 @@ def test_nl_forces_match_oracle(name, precision, form, monkeypatch):
     tol = FP64_FORCE if precision == SQ_FP64 else FP32_FORCE
     np.testing.assert_allclose(F, F_ref, rtol=0, atol=tol * scale)
     F2 = solver.nl_forces(_dev(s.V), mu, wl.kT, chi=_dev(chi), zeta=_dev(zeta)).cpu().numpy()
-    assert np.array_equal(F, F2)                                   # fixed-order sums: repeats bit for bit
+    if precision == SQ_FP64 or form != "region":
+        assert np.array_equal(F, F2)                               # fixed-order sums: repeats bit for bit
+    else:                                                          # FP32 shared-memory atomics in the update
+        assert np.abs(F - F2).max() <= 1e-5 * scale
     solver.close()
 
 
