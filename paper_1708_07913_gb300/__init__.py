@@ -197,6 +197,9 @@ class SQSCF:
         ``fresh_below`` = r ends the reuse once the residual is at or below
         r: from then on every iteration takes fresh bounds, and the loop ends
         on the fixed point of SQ with bounds of (nearly) its own potential.
+        That changes the map the mixer iterates, so the mixing history is
+        dropped at the switch (its differences belong to the old map; kept,
+        they stalled Anderson mixing at the jump in the residual).
         ``refine`` = (solver_fp64, r_switch): once the residual is at or below
         r_switch, the remaining iterations run on solver_fp64 (an FP64
         context of the same grid and atoms), starting from the current bounds
@@ -247,15 +250,19 @@ class SQSCF:
         ref = None                                   # (V_ref, chi_ref, zeta_ref) of the last Lanczos run
         lanczos = 0
         refined_at = None
+        reusing = self.reuse is not None             # still in the bound-reuse phase
         for it in range(len(res), max_iter):
             if self.refine is not None and refined_at is None and res and res[-1] <= self.refine[1]:
                 fine = self.refine[0]
                 fine.chi.copy_(sv.chi)
                 fine.zeta.copy_(sv.zeta)
                 sv, refined_at = fine, it
+            switched = False
+            if reusing and self.fresh_below is not None and res and res[-1] <= self.fresh_below:
+                reusing, switched = False, True      # the reuse ends for good
             if refined_at is not None:
                 w_max = 1e-3
-            elif self.reuse is not None and not (self.fresh_below is not None and res and res[-1] <= self.fresh_below):
+            elif reusing:
                 w_max = self.reuse
             else:
                 w_max = None                         # fresh bounds this iteration
@@ -276,6 +283,8 @@ class SQSCF:
             k, _ = sq.sq_poisson(sv.ctx, sv.rho, self.phi, poisson_tol)
             pit.append(k)
             sq.sq_effective_potential(sv.ctx, self.V_loc, self.phi, sv.rho, self.alpha, self.V_out)
+            if switched:
+                sq.sq_mixer_reset(self.mixer)
             if self.kerker is None:
                 res.append(sq.sq_mixer_step(self.mixer, V_in, self.V_out, V_next))
             else:

@@ -147,6 +147,30 @@ def test_widen_bounds_and_scf_that_reuses_them():
     solver.close()
 
 
+def test_scf_that_stops_reusing_bounds_reaches_the_fresh_fixed_point():
+    """Bounds reused (widened by the potential change, up to 0.05 Ha) while
+    the residual is above 1e-4, fresh from then on, with the mixing history
+    dropped at the switch: the loop converges to 1e-9 and lands on the fixed
+    point of the SCF that takes fresh bounds every iteration (FP64: to the
+    residual left), not on the one of the reused bounds."""
+    wl = synth.custom_workload("scf8s", cells=1, n=8, r_cut=2.5, npl=24, kT=0.1, sigma_disp=0.1, nonlocal_=True,
+                               seed=1744)
+    s = synth.make_system(wl)
+    V_loc = _dev(s.V)
+    solver = SQSolver.from_workload(wl, s.positions, precision=SQ_FP64, device=DEV)
+    fresh = SQSCF(solver, V_loc, wl.n_electrons, wl.kT).run(tol=1e-9, max_iter=80)
+    rho_fresh, mu_fresh = fresh["rho"].cpu().numpy().copy(), fresh["mu"]
+    mixed = SQSCF(solver, V_loc, wl.n_electrons, wl.kT, reuse_bounds=0.05, fresh_below=1e-4).run(tol=1e-9,
+                                                                                                 max_iter=80)
+    assert fresh["converged"] and mixed["converged"]
+    assert mixed["lanczos_runs"] < mixed["iterations"]
+    np.testing.assert_allclose(mixed["rho"].cpu().numpy(), rho_fresh, rtol=0, atol=1e-6 * np.abs(rho_fresh).max())
+    assert abs(mixed["mu"] - mu_fresh) < 1e-7
+    print(f"SCF to 1e-9: fresh bounds {fresh['iterations']} iterations; reuse until 1e-4, then fresh: "
+          f"{mixed['iterations']} ({mixed['lanczos_runs']} Lanczos runs)")
+    solver.close()
+
+
 def test_fp32_scf_refined_in_fp64_reaches_the_fp64_fixed_point():
     """FP32 iterations until the residual is 1e-5, then an FP64 context of
     the same grid and atoms takes over with the mixing history: the loop
