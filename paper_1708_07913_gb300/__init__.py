@@ -203,9 +203,11 @@ class SQSCF:
         ``refine`` = (solver_fp64, r_switch): once the residual is at or below
         r_switch, the remaining iterations run on solver_fp64 (an FP64
         context of the same grid and atoms), starting from the current bounds
-        and keeping the mixing history; they reuse the last Lanczos bounds
-        widened by the potential change while that stays within 1e-3 Ha (an
-        FP64 Lanczos run costs about two FP64 SQ steps).  The FP32 recurrence
+        with a fresh mixing history (the FP32 map's differences in the
+        history kept the loop wandering at the FP32 noise level for as many
+        iterations as the history is long); they reuse the last Lanczos
+        bounds widened by the potential change while that stays within 1e-3
+        Ha (an FP64 Lanczos run costs about two FP64 SQ steps).  The FP32 recurrence
         leaves rounding noise of ~1e-6 relative in the density, which stalls
         the residual near that level; the FP64 iterations converge past it."""
         torch = solver.torch
@@ -252,12 +254,12 @@ class SQSCF:
         refined_at = None
         reusing = self.reuse is not None             # still in the bound-reuse phase
         for it in range(len(res), max_iter):
+            switched = False
             if self.refine is not None and refined_at is None and res and res[-1] <= self.refine[1]:
                 fine = self.refine[0]
                 fine.chi.copy_(sv.chi)
                 fine.zeta.copy_(sv.zeta)
-                sv, refined_at = fine, it
-            switched = False
+                sv, refined_at, switched = fine, it, True
             if reusing and self.fresh_below is not None and res and res[-1] <= self.fresh_below:
                 reusing, switched = False, True      # the reuse ends for good
             if refined_at is not None:
