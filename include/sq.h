@@ -205,12 +205,18 @@ int sq_density_energy_noalloc(int n1, int n2, int n3, double h, int npl,
  *              overwritten; may be NULL when the context has no projectors
  * The recurrence vectors, D and the projector inner products are in the
  * context's precision (FP32 or FP64); the coefficients c^j and the final
- * contraction are FP64.  The result repeats bit for bit on a given GPU.
- * Allocates, on first use, about 2 x SMs x (4 s (2m+1)^3 + (384 + 128 s)
- * (2m+1)^2 + (24 + 4 s) ccap + 24 n_atoms) bytes of workspace in the context
- * (s = 4 or 8 bytes).  A region row crossed by more than 32 projector
- * supports returns SQ_ECAPACITY.
- * Synchronises the stream; a projector-table overflow returns SQ_ECAPACITY. */
+ * contraction are FP64.  The recurrence runs on the machinery of the region
+ * kernels (one CTA per node, vectors in shared memory); in FP32 its
+ * projector update adds with shared-memory atomics, so repeated calls agree
+ * to FP32 rounding, and FP64 results repeat bit for bit.  Where that form
+ * does not fit the context (or with SQ_FORCE_KERNEL=legacy in the
+ * environment) a first form with every vector in global scratch runs, which
+ * repeats bit for bit in both precisions.  Allocates, on first use, about
+ * (resident CTAs) x (s (2m+1)^3 + 12 KB + 24 n_atoms) bytes of workspace in
+ * the context (s = 4 or 8 bytes; the first form: 2 x SMs x (4 s (2m+1)^3 +
+ * (384 + 128 s) (2m+1)^2 + (24 + 4 s) ccap + 24 n_atoms)).
+ * Synchronises the stream; a projector-table overflow (more candidates or
+ * row entries than the tables hold) returns SQ_ECAPACITY. */
 int sq_nl_forces(sq_ctx *ctx, const double *V, const double *chi, const double *zeta,
                  double mu, double kT, double *forces);
 
