@@ -75,7 +75,7 @@ def parse():
     p.add_argument("--save-rho", default="", help="write the last step's density (float32 .npy) to this path")
     p.add_argument("--fresh-below", default="none",
                    help="scf_*, warmstart_c4: residual below which bounds are no longer reused (none: reuse to the end)")
-    p.add_argument("--refine-at", default="none",
+    p.add_argument("--refine-at", default="1e-5",
                    help="scf_*, warmstart_c4: residual at which an FP64 context takes over (none: FP32 throughout)")
     p.add_argument("--batch-plan", choices=["auto", "streams", "share", "queue"], default="auto",
                    help="batch16: launch plan (auto: the autotuner times them and keeps the fastest)")
