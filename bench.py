@@ -16,11 +16,15 @@ error against the FP64 result.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
                   [--workload al108_48|al2048_128|...] [--impl reference]
-  python bench.py --workload batch16          (16 uneven systems as one CUDA graph)
+  python bench.py --workload batch16          (16 uneven systems as one CUDA graph;
+                                               --batch-plan auto|streams|share|queue, --nodes-per-item k)
   python bench.py --workload force_al108_48   (nonlocal atomic forces; --precision fp32|fp64)
-  python bench.py --workload scf_al256_64     (SCF to 1e-6: Kerker-preconditioned Anderson mixing)
+  python bench.py --workload scf_al256_64     (SCF to 1e-6: Kerker-preconditioned Anderson mixing,
+                                               FP32 then FP64 from --refine-at 1e-5; --reuse-bounds w,
+                                               --fresh-below r)
   python bench.py --workload warmstart_c4     (train the warm-start network, then SCF
                                                iterations to 1e-6 on al256_64 with and without it)
+  python bench.py --n-lanczos K --margin M    (ablation of the bounds' cost; --save-rho path)
 
 Under torchrun (N > 1) every rank runs an independent replica of the workload
 on its own GPU (the path has no data exchange between replicas); the JSON line
